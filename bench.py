@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark of the WENO-ZA6 hot path on GB300.
+
+One benchmark step = one SSP-RK3 step (three right-hand-side stages: GLF
+splitting, Roe characteristic projection, WENO-ZA6 reconstruction, flux
+difference, stage combination, CFL reduction) of 2D Euler on the seeded
+four-quadrant workload, 2048 x 2048 cells, FP64.  The metric is cell-updates
+per second (one cell advanced one full Runge-Kutta step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+paper) on the host cores, on a bounded window of the same workload.
+Under torchrun (N > 1) every rank advances its own replica (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D Euler cell-updates/s FP64 vs FP32-recon; batched-solve p50/p99 latency"
+UNIT = "cell-updates/s"
+N_GRID = 2048
+SEED = 3
+
+# FP64 floating-point operations of one stage launch per cell, counted from
+# the kernel's arithmetic (fma = 2, add/mul/div/sqrt/rsqrt = 1; abs, compare
+# and integer work not counted).  Per interface (2D, one direction):
+#   Roe average and eigen-system 23, projection of 6 states and 6 fluxes 180,
+#   GLF split 96, 8 WENO-ZA6 reconstructions x 105 = 840, sums 4,
+#   back-projection 21  -> 1164.
+# Per cell: primitives and fluxes 20, flux difference 20, Runge-Kutta
+# combination 20, next-stage wavespeeds 18 -> 78.
+# Two interfaces per cell (x and y): 2 * 1164 + 78 = 2406.
+FLOPS_PER_FACE = 1164
+FLOPS_PER_CELL = 78
+FLOPS_PER_CELL_STAGE = 2 * FLOPS_PER_FACE + FLOPS_PER_CELL
+# FP64 peak: the nominal GB300 figure, 1.25 TFLOP/s (152 SMs x 2 FP64 FMA
+# lanes x 2 flop x ~2.06 GHz).
+FP64_PEAK_TFLOPS = 1.25
+KERNEL_SOURCES = ["paper_2603_26272_gb300/csrc/weno_kernels.cu",
+                  "paper_2603_26272_gb300/csrc/weno_device.cuh"]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per stage launch from the committed ncu capture, if it was
+    taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_hash") != kernel_hash():
+        return None
+    return rec.get("dram_bytes_per_launch_2048")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.fh = None
+
+    def start(self):
+        try:
+            self.fh = tempfile.TemporaryFile(mode="w+")
+            cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.fh.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(seconds, window=256):
+    """The oracle, as it stands, on a window of the bench workload (the
+    window around the quadrant corner, as its own problem with transmissive
+    boundaries; the oracle's cost per cell does not depend on the data)."""
+    import oracle
+    from paper_2603_26272_gb300 import workloads as wl
+    w = wl.quadrant_2d(n=N_GRID, seed=SEED)
+    c0 = N_GRID // 2 - window // 2
+    U = np.ascontiguousarray(w["U"][:, :, c0:c0 + window, c0:c0 + window])
+    g = oracle.make_grid(ndim=2, nx=window, ny=window, dx=w["dx"], dy=w["dy"])
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        dt = oracle.cfl_dt(g, U, 0.5)
+        U = oracle.ssprk3_step(g, U, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": window * window * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d x %d window of the 2048^2 quadrant workload (centred on the quadrant "
+                      "corner), %d SSP-RK3 steps, single-threaded C++ oracle, %.1f s"
+                      % (window, window, steps, el)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2603_26272_gb300 import workloads as wl
+    window = 256
+    w = wl.quadrant_2d(n=N_GRID, seed=SEED)
+    c0 = N_GRID // 2 - window // 2
+    U = np.ascontiguousarray(w["U"][:, :, c0:c0 + window, c0:c0 + window])
+    g = oracle.make_grid(ndim=2, nx=window, ny=window, dx=w["dx"], dy=w["dy"])
+    for _ in range(args.warmup):
+        U = oracle.ssprk3_step(g, U, oracle.cfl_dt(g, U, 0.5))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = oracle.ssprk3_step(g, U, oracle.cfl_dt(g, U, 0.5))
+    el = time.perf_counter() - t0
+    value = window * window * args.steps / el
+    sample = ("%d x %d window of the 2048^2 quadrant workload per step, single-threaded C++ "
+              "oracle" % (window, window))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "2D Euler four-quadrant Riemann data (seed 3), %dx%d window "
+                                  "of the 2048x2048 grid, FP64, SSP-RK3 CFL 0.5" % (window, window),
+                      "l2": "host run"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_2603_26272_gb300 import weno
+    from paper_2603_26272_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    n = args.n
+    w = wl.quadrant_2d(n=n, seed=SEED)
+    d = weno.desc_for(w)
+    U0 = torch.from_numpy(w["U"])
+    U = U0.cuda()
+    ws = weno.workspace(d, host=True)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        weno.step(d, U, ws=ws, sync=False)
+    weno.sync_status(d, ws)
+
+    # alpha-only launch time (the wavespeed pass that opens every step)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    weno.wavespeeds(d, U, ws=ws)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(5):
+        weno.wavespeeds(d, U, ws=ws)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    alpha_ms = ev[0].elapsed_time(ev[1]) / 5
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
+    except Exception:
+        gpu_id = local
+    clocks = Clocks(gpu_id)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        weno.step(d, U, ws=ws, sync=False)
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    elapsed_ms = start.elapsed_time(end)
+    weno.sync_status(d, ws)
+    t_max = elapsed_ms
+    if dist:
+        tt = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    cells = n * n
+    value = world * cells * args.steps / (t_max / 1e3)
+    ms_step = t_max / args.steps
+
+    # end to end: the public host-buffer call, H2D + step + D2H per step
+    H = U0.clone().pin_memory()
+    weno.step_host(d, H, ws=ws)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        weno.step_host(d, H, ws=ws)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    state_bytes = U0.numel() * 8
+
+    stage_ms = (ms_step - alpha_ms) / 3.0
+    flops = cells * FLOPS_PER_CELL_STAGE
+    achieved = flops / (stage_ms / 1e3) / 1e12
+    traffic = ncu_traffic()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D Euler %dx%d four-quadrant Riemann data (seed %d, rho,p~U[0.1,1.5], "
+                               "u,v~U[-1,1]), transmissive, FP64, WENO-ZA6 Ai-Z p=1, SSP-RK3 CFL 0.5"
+                               % (n, n, SEED, ),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (state %.0f MB, working set %.0f MB)"
+                         % (state_bytes / 1e6, 3 * state_bytes / 1e6)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "k_euler2d stage launch", "stage_ms": stage_ms,
+                     "alpha_ms": alpha_ms, "flops_per_launch": flops,
+                     "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s), see DESIGN.md"},
+        "e2e": {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        log("timing the CPU oracle on the host cores ...")
+        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

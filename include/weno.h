@@ -1,0 +1,158 @@
+/*
+ * weno.h -- C-ABI of libweno: the WENO-ZA6 finite-difference right-hand side
+ * and third-order SSP Runge-Kutta stepping, in CUDA for GB300 (sm_103a).
+ *
+ * Method: Gu, Wang, Don, Jung, "A Family of Even-Order Central-Upwind WENO
+ * Schemes with Averaged Downwind and Novel Global Smoothness Indicators",
+ * arXiv 2603.26272.  The sixth-order scheme WENO-ZA6 is Section 3; its
+ * ingredients are the general framework of Section 2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * State layout: U is a contiguous array of doubles [nbatch][ncomp][ny][nx],
+ *   x fastest, holding nbatch independent problems of the same shape.
+ *   ncomp = 1 for scalar advection (u), 3 for 1D Euler (rho, rho u, E),
+ *   4 for 2D Euler (rho, rho u, rho v, E); ny = 1 in 1D.  Cells are uniform:
+ *   dx = (x1 - x0) / nx, dy = (y1 - y0) / ny (Section 2: x_{i+1/2} = a + i dx).
+ * Memory: every array argument named U, dUdt, alpha or ws is DEVICE memory
+ *   owned by the caller (for instance a PyTorch tensor), except where an
+ *   entry point says "host".  The library never allocates device memory;
+ *   scratch space is the caller's workspace `ws` of at least
+ *   weno_workspace_bytes(d) bytes, 256-byte aligned, passed with its size.
+ *   A workspace may be reused by consecutive calls on one stream; calls that
+ *   share a workspace must not run concurrently.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *   work is enqueued on it; entry points that return values to the host
+ *   synchronise that stream and say so.
+ * Errors: every entry point returns a weno_status and never aborts.  On an
+ *   error, weno_last_error() returns a message for the calling host thread.
+ *   Device-side failures (a nonphysical state: rho <= 0, p <= 0, a
+ *   non-positive Roe sound speed or a non-finite value) are recorded in the
+ *   workspace and reported at the next synchronising call.
+ */
+#ifndef WENO_H
+#define WENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WENO_OK = 0,
+  WENO_ERR_ARG = 1,         /* invalid descriptor, pointer or size            */
+  WENO_ERR_CUDA = 2,        /* a CUDA runtime call failed                     */
+  WENO_ERR_NONPHYSICAL = 3, /* rho <= 0, p <= 0, c^2 <= 0 or non-finite met   */
+  WENO_ERR_NOMEM = 4,       /* workspace smaller than weno_workspace_bytes    */
+  WENO_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                  */
+  WENO_ERR_MAXSTEPS = 6     /* weno_solve stopped at max_steps before t_final */
+} weno_status;
+
+enum { WENO_SYS_ADVECTION = 0, WENO_SYS_EULER = 1 };
+enum { WENO_BC_TRANSMISSIVE = 0, WENO_BC_PERIODIC = 1 };
+enum { WENO_PREC_FP64 = 0, WENO_PREC_FP32_RECON = 1 };
+enum { WENO_ALPHA_FIELD = 0, WENO_ALPHA_SINGLE = 1 };
+
+/* Problem descriptor.  Defaults of the paper: eps = 1e-40 (Section 4
+ * preamble), mu0 = 1e-40 (eq. (22)), p = 1 (Section 4 preamble; L = q = 1
+ * are fixed, Section 2.1 after Table 1), gamma = 1.4 (Section 4.2). */
+typedef struct weno_desc {
+  int32_t system;     /* WENO_SYS_ADVECTION (u_t + a u_x = 0) or WENO_SYS_EULER   */
+  int32_t ndim;       /* 1 or 2 (advection: 1)                                    */
+  int64_t nbatch;     /* number of independent problems, >= 1                     */
+  int64_t nx, ny;     /* cells per axis, nx >= 1, ny >= 1 (ny = 1 when ndim = 1)  */
+  double x0, x1;      /* domain [x0, x1]                                          */
+  double y0, y1;      /* domain [y0, y1] (ignored in 1D)                          */
+  int32_t bc_x, bc_y; /* WENO_BC_*: 3 ghost cells per side, zero-gradient or wrap */
+  double gamma;       /* ratio of specific heats (Euler)                          */
+  double cfl;         /* CFL number of the time step rule                         */
+  double eps;         /* sensitivity epsilon of eq. (21)                          */
+  double mu0;         /* mu_0 of eq. (22)                                         */
+  double p;           /* power parameter p of eq. (21), >= 1                      */
+  int32_t ai;         /* 1: affine-invariant descaler mu[f] of eq. (22); 0: mu = 1 */
+  int32_t precision;  /* WENO_PREC_FP64 (FP32_RECON is reserved)                  */
+  int32_t alpha_mode; /* WENO_ALPHA_FIELD: GLF speed per characteristic field;    */
+                      /* WENO_ALPHA_SINGLE: one speed max|u|+c for all fields     */
+  int32_t reserved;   /* must be 0                                                */
+  double adv_speed;   /* a of the advection equation                              */
+} weno_desc;
+
+/* Bytes of device workspace that weno_rhs / weno_step / weno_solve need for d:
+ * two stage states, the reduction slots and the per-problem clocks.  Returns
+ * 0 if d is invalid (see weno_last_error). */
+size_t weno_workspace_bytes(const weno_desc *d);
+
+/* Global Lax-Friedrichs speeds of eq. (6) for the state U:
+ * alpha[b*8 + dir*4 + m] = max over all cells of problem b of |lambda_m|
+ * (dir 0 = x, 1 = y; m = characteristic field in the order u-c, u, u(, u+c);
+ * unused slots 0), and the CFL time step dt[b] (1D: cfl dx / max(|u|+c);
+ * 2D: cfl / (max(|u|+c)/dx + max(|v|+c)/dy); advection: cfl dx / |a|).
+ * alpha and dt are DEVICE arrays of nbatch*8 and nbatch doubles.
+ * Asynchronous. */
+weno_status weno_wavespeeds(const weno_desc *d, const double *U, double *alpha, double *dt,
+                            void *ws, size_t ws_bytes, void *stream);
+
+/* Right-hand side of one Runge-Kutta stage, L(U) (eq. (5) dimension by
+ * dimension: dU/dt = -(F_{i+1/2} - F_{i-1/2})/dx - (G_{j+1/2} - G_{j-1/2})/dy),
+ * with the interface fluxes of WENO-ZA6 (Section 3) after global
+ * Lax-Friedrichs splitting (eq. (6)), characteristic-wise on Roe-averaged
+ * eigenvectors for Euler (Section 4.2), and the GLF speeds taken from U.
+ * dUdt has U's layout and must not overlap U.  Asynchronous. */
+weno_status weno_rhs(const weno_desc *d, const double *U, double *dUdt, void *ws,
+                     size_t ws_bytes, void *stream);
+
+/* One third-order SSP (TVD) Runge-Kutta step of every problem, in place
+ * (Section 4 preamble):
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+ *   U <- 1/3 U + 2/3 (U2 + dt L(U2)).
+ * dt > 0: that step for every problem; dt <= 0: each problem's own CFL step
+ * (as in weno_wavespeeds).  dt_used: NULL (asynchronous call) or a HOST
+ * array of nbatch doubles that receives the steps taken; then the call
+ * synchronises the stream and also reports device-side errors. */
+weno_status weno_step(const weno_desc *d, double *U, double dt, double *dt_used, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/* Advance every problem from t0 to t_final with CFL steps, clipping each
+ * problem's last step to land on t_final, taking at most max_steps steps.
+ * t_out / steps_out: HOST arrays of nbatch (may be NULL) receiving each
+ * problem's reached time and step count.  Synchronises the stream.
+ * Returns WENO_ERR_MAXSTEPS if a problem had not reached t_final; on
+ * WENO_ERR_NONPHYSICAL, U holds the state in which the bad value appeared. */
+weno_status weno_solve(const weno_desc *d, double *U, double t0, double t_final,
+                       int64_t max_steps, double *t_out, int64_t *steps_out, void *ws,
+                       size_t ws_bytes, void *stream);
+
+/* weno_step on a HOST state: copies U_host (nbatch*ncomp*ny*nx doubles) to
+ * the device, takes one step as weno_step does, and copies the result back
+ * into U_host.  The workspace must hold weno_workspace_bytes_host(d) bytes.
+ * dt_used: NULL or a HOST array of nbatch doubles.  Synchronises the stream. */
+weno_status weno_step_host(const weno_desc *d, double *U_host, double dt, double *dt_used,
+                           void *ws, size_t ws_bytes, void *stream);
+
+/* weno_solve on a HOST state: copies U_host to the device, solves, copies the
+ * result back into U_host.  The workspace must hold
+ * weno_workspace_bytes_host(d) bytes (the device copy of U lives there).
+ * U_host may be pageable, but pinned memory gives full copy bandwidth.
+ * Synchronises the stream. */
+size_t weno_workspace_bytes_host(const weno_desc *d);
+weno_status weno_solve_host(const weno_desc *d, double *U_host, double t0, double t_final,
+                            int64_t max_steps, double *t_out, int64_t *steps_out, void *ws,
+                            size_t ws_bytes, void *stream);
+
+/* Synchronise the stream and report the device-side status recorded in the
+ * workspace by the previous asynchronous calls (WENO_OK or
+ * WENO_ERR_NONPHYSICAL with the problem, cell and stage in weno_last_error). */
+weno_status weno_sync_status(const weno_desc *d, void *ws, size_t ws_bytes, void *stream);
+
+/* Message describing the last error on the calling host thread ("" if none). */
+const char *weno_last_error(void);
+
+/* Library version string. */
+const char *weno_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WENO_H */

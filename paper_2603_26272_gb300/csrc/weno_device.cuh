@@ -1,0 +1,195 @@
+// weno_device.cuh -- device building blocks of the WENO-ZA6 right-hand side.
+//
+// Method: Gu, Wang, Don, Jung, arXiv 2603.26272 (WENO-ZA6, Section 3; the
+// general framework of Section 2; the Euler systems of Section 4).
+//
+// Arithmetic economy.  On GB300 the FP64 pipe is ~1/64 of the FP32 rate, so
+// this path is bound by FP64 instruction issue, not by HBM.  Every formula
+// below is an algebraically exact rewrite of the paper's, chosen to use few
+// FP64 operations and to round relative to the stencil's variation:
+//  * the smoothness indicators of eq. (15) in terms of first and second
+//    differences (equal to the quadratic forms <f_k, B_k f_k>),
+//  * tau of eq. (17) as a third difference of second differences,
+//  * the candidate fluxes of eq. (11) as f_i plus a difference correction,
+//  * the left eigenvectors of the Roe matrix in closed form with shared
+//    sub-expressions, two of their rows and the 1/2 of eq. (6) folded into
+//    the back-projection.
+#pragma once
+#include <cstdint>
+
+namespace weno {
+
+// Parameters of eqs. (21)-(22) for one characteristic field.  The field's
+// split fluxes reach the reconstruction multiplied by `scale` (2 or 4, see
+// the projection below), so mu_0 and, without Ai, epsilon are scaled to keep
+// Gamma_k exactly the paper's.
+struct ReconParams {
+  double eps4;   // 4 * eps            (indicators are carried as 4*beta, 4*tau)
+  double mu0s;   // scale * mu_0       (Ai)
+  double efix;   // 4 * eps * scale^2  (no Ai: mu = 1)
+  double p;      // power parameter of eq. (21)
+};
+
+// f > 0 and finite, by the bit pattern (integer pipe only).
+__device__ __forceinline__ bool pos_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7FF0000000000000LL;
+}
+
+// Bit pattern of |x| as an ordered integer: for non-negative doubles the
+// integer order is the numeric order (NaN sorts above +inf).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+// ---------------------------------------------------------------------------
+// WENO-ZA6 numerical flux at x_{i+1/2} from v0..v5 = f_{i-2}..f_{i+3}
+// (positive flux; the negative flux is this routine on the mirrored stencil).
+//
+// With d_j = v_{j+1} - v_j and s_k = d_{k+1} - d_k:
+//   4 beta_k = 13/3 s_k^2 + t_k^2, t = (3d1 - d0, d1 + d2, 3d2 - d3, 3d4 - 5d3)
+//       (eq. (15) with the matrices B_0, B_1, B_2 = rev(B_0), B_d),
+//   4 beta_3 = mean of the four (eq. (16)),
+//   4 tau = 4 (s3 - s0 + 3 (s1 - s2))^2 (eq. (17): the fifth difference),
+//   f^k = v2 + r_k / 6, r = (5d1 - 2d0, d1 + 2d2, 4d2 - d3, 6d2 - 5d3 + 2d4)
+//       (eq. (11)),
+//   mu = mean |v_j - mean v| + mu_0 (eq. (22)), Gamma_k = (tau/(beta_k +
+//   eps mu^2))^p (eq. (21)), alpha_k = d_k (1 + Gamma_k) (eq. (20), L = q = 1),
+//   f = sum alpha_k f^k / sum alpha_k (eqs. (14), (19)), d = (1, 9, 9, 1)/20.
+// ---------------------------------------------------------------------------
+template <bool AI, bool P1>
+__device__ __forceinline__ double za6(double v0, double v1, double v2, double v3, double v4,
+                                      double v5, const ReconParams &P) {
+  const double d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3, d4 = v5 - v4;
+  const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
+  const double t0 = fma(3.0, d1, -d0);
+  const double t1 = d1 + d2;
+  const double t2 = fma(3.0, d2, -d3);
+  const double t3 = fma(3.0, d4, -5.0 * d3);
+  const double c13 = 13.0 / 3.0;
+  const double B0 = fma(c13 * s0, s0, t0 * t0);
+  const double B1 = fma(c13 * s1, s1, t1 * t1);
+  const double B2 = fma(c13 * s2, s2, t2 * t2);
+  const double Bd = fma(c13 * s3, s3, t3 * t3);
+  const double B3 = 0.25 * ((B0 + B1) + (B2 + Bd));
+  const double r5 = fma(3.0, s1 - s2, s3 - s0);
+  const double T = 4.0 * (r5 * r5);
+  double e;
+  if (AI) {
+    // deviations from the stencil mean, formed from the differences
+    const double a0 = -(d0 + d1), a1 = -d1, a3 = d2, a4 = d2 + d3, a5 = a4 + d4;
+    const double m = ((a0 + a1) + (a3 + a4) + a5) * (1.0 / 6.0);
+    const double dev = fabs(a0 - m) + fabs(a1 - m) + fabs(m) + fabs(a3 - m) + fabs(a4 - m) +
+                       fabs(a5 - m);
+    const double mu = fma(dev, 1.0 / 6.0, P.mu0s);
+    e = P.eps4 * (mu * mu);
+  } else {
+    e = P.efix;
+  }
+  double g0 = T / (B0 + e), g1 = T / (B1 + e), g2 = T / (B2 + e), g3 = T / (B3 + e);
+  if (!P1) {
+    g0 = pow(g0, P.p);
+    g1 = pow(g1, P.p);
+    g2 = pow(g2, P.p);
+    g3 = pow(g3, P.p);
+  }
+  const double a0 = 1.0 + g0, a1 = 9.0 * (1.0 + g1), a2 = 9.0 * (1.0 + g2), a3 = 1.0 + g3;
+  const double r0 = fma(5.0, d1, -2.0 * d0);
+  const double r1 = fma(2.0, d2, d1);
+  const double r2 = fma(4.0, d2, -d3);
+  const double r3 = fma(6.0, d2, fma(-5.0, d3, 2.0 * d4));
+  const double num = fma(a0, r0, fma(a1, r1, fma(a2, r2, a3 * r3)));
+  const double den = 6.0 * ((a0 + a1) + (a2 + a3));
+  return v2 + num / den;
+}
+
+// ---------------------------------------------------------------------------
+// Characteristic-wise Lax-Friedrichs flux of the Euler equations at one face
+// (Section 4.2), in the face's normal frame: components (rho, m_n, m_t, E)
+// with normal flux (F0..F3), face-normal velocity u_n, tangential u_t.
+//
+// Roe average of the cells on both sides; right eigenvectors
+//   r1 = (1, un-c, ut, H-un c), r2 = (1, un, ut, q^2/2), r3 = (0, 0, 1, ut),
+//   r4 = (1, un+c, ut, H+un c);
+// with b1 = (gamma-1)/c^2, b2 = b1 q^2/2, the left eigenvectors are
+//   l1 = 1/2 (b2 + un/c, -(b1 un + 1/c), -b1 ut, b1),  l2 = (1-b2, b1 un, b1 ut, -b1),
+//   l3 = (-ut, 0, 1, 0),  l4 = 1/2 (b2 - un/c, -(b1 un - 1/c), -b1 ut, b1).
+// The kernel projects with 2 l1, l2, l3, 2 l4 and splits without the 1/2 of
+// eq. (6), so field m reaches the reconstruction scaled by k = (4, 2, 2, 4);
+// the back-projection divides again.
+// ---------------------------------------------------------------------------
+struct FaceState {
+  double un, ut, H, c, ic, b1, b2, hq2;  // Roe-averaged face state
+};
+
+__device__ __forceinline__ bool roe_face(double sl, double unl, double utl, double Hl, double sr,
+                                         double unr, double utr, double Hr, double gm1,
+                                         FaceState &f) {
+  const double inv = 1.0 / (sl + sr);
+  const double wl = sl * inv, wr = sr * inv;
+  f.un = fma(wl, unl, wr * unr);
+  f.ut = fma(wl, utl, wr * utr);
+  f.H = fma(wl, Hl, wr * Hr);
+  const double q2 = fma(f.un, f.un, f.ut * f.ut);
+  f.hq2 = 0.5 * q2;
+  const double c2 = gm1 * (f.H - f.hq2);
+  if (!pos_finite(c2)) return false;
+  f.ic = rsqrt(c2);
+  f.c = c2 * f.ic;
+  f.b1 = gm1 * (f.ic * f.ic);
+  f.b2 = f.b1 * f.hq2;
+  return true;
+}
+
+// Characteristic values (2 l1.V, l2.V, l3.V, 2 l4.V) of a vector V in the
+// normal frame (rho-like, mn-like, mt-like, E-like).
+__device__ __forceinline__ void project4(const FaceState &f, double r, double mn, double mt,
+                                         double E, double &w1, double &w2, double &w3,
+                                         double &w4) {
+  const double s = fma(f.un, mn, fma(f.ut, mt, -E));
+  const double z = fma(f.b2, r, -(f.b1 * s));
+  const double tc = fma(f.un, r, -mn) * f.ic;
+  w1 = z + tc;
+  w4 = z - tc;
+  w2 = r - z;
+  w3 = fma(-f.ut, r, mt);
+}
+
+// Physical flux from h = (h1, h2, h3, h4) reconstructed in the scaled
+// characteristic fields: e = (h1/4, h2/2, h3/2, h4/4) then F = R e.
+__device__ __forceinline__ void backproject4(const FaceState &f, double h1, double h2, double h3,
+                                             double h4, double &F0, double &F1, double &F2,
+                                             double &F3) {
+  const double e1 = 0.25 * h1, e2 = 0.5 * h2, e3 = 0.5 * h3, e4 = 0.25 * h4;
+  const double S = (e1 + e4) + e2;
+  const double D = e4 - e1;
+  F0 = S;
+  F1 = fma(f.un, S, f.c * D);
+  F2 = fma(f.ut, S, e3);
+  F3 = fma(f.H, e1 + e4, fma(f.un * f.c, D, fma(f.hq2, e2, f.ut * e3)));
+}
+
+// 1D Euler (rho, m, E): R = [(1, u-c, H-uc), (1, u, u^2/2), (1, u+c, H+uc)],
+// L rows 1/2 (b2 + u/c, -(b1 u + 1/c), b1), (1-b2, b1 u, -b1),
+// 1/2 (b2 - u/c, -(b1 u - 1/c), b1); fields scaled by k = (4, 2, 4).
+__device__ __forceinline__ void project3(const FaceState &f, double r, double m, double E,
+                                         double &w1, double &w2, double &w3) {
+  const double s = fma(f.un, m, -E);
+  const double z = fma(f.b2, r, -(f.b1 * s));
+  const double tc = fma(f.un, r, -m) * f.ic;
+  w1 = z + tc;
+  w3 = z - tc;
+  w2 = r - z;
+}
+
+__device__ __forceinline__ void backproject3(const FaceState &f, double h1, double h2, double h3,
+                                             double &F0, double &F1, double &F2) {
+  const double e1 = 0.25 * h1, e2 = 0.5 * h2, e3 = 0.25 * h3;
+  const double S = (e1 + e3) + e2;
+  const double D = e3 - e1;
+  F0 = S;
+  F1 = fma(f.un, S, f.c * D);
+  F2 = fma(f.H, e1 + e3, fma(f.un * f.c, D, f.hq2 * e2));
+}
+
+}  // namespace weno

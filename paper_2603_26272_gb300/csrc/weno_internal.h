@@ -1,0 +1,62 @@
+// weno_internal.h -- launch interface between the C-ABI layer and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace weno {
+
+// Device status word and the location of the first failure.
+struct DevStatus {
+  int code;      // 0 ok, 3 nonphysical
+  int stage;     // kernel that recorded it (0 wavespeeds, 1..3 RK stage, 4 rhs)
+  long long b, j, i;
+};
+
+// Everything one stage launch needs (passed by value).
+struct StageArgs {
+  // grid
+  int system, ndim, nc;
+  long long nbatch, nx, ny;
+  double dx, dy;
+  int bc_x, bc_y;
+  double gamma;
+  // scheme
+  double cfl, eps, mu0, p;
+  int ai, alpha_single;
+  double adv_speed;
+  // data
+  const double *Uin;  // stage input (read with the stencil)
+  const double *Un;   // base of the RK combination (read at the own cell only)
+  double *Uout;       // may alias Un (last stage)
+  double a_n, a_s;    // Uout = a_n Un + a_s (Uin + dt L(Uin))
+  int mode;           // 0 RK stage, 1 write L(Uin)
+  int stage;          // 1, 2, 3 (1 sets dt, 3 advances t) ; 0 for rhs
+  double dt_fixed;    // > 0: fixed step for stage 1
+  double t_final;     // clipping target of stage 1 (inf: none)
+  // workspace
+  const unsigned long long *alpha_in;  // [nbatch][8] bit patterns of |lambda| maxima
+  unsigned long long *alpha_out;       // next stage's maxima (NULL: skip)
+  unsigned long long *alpha_zero;      // slot to clear for the stage after next (NULL: skip)
+  double *t, *tnext, *dt;              // [nbatch]
+  long long *steps;                    // [nbatch]
+  DevStatus *status;
+};
+
+// Wavespeed reduction of U into alpha_out (which must be zero), optional dt.
+struct AlphaArgs {
+  int system, ndim, nc;
+  long long nbatch, nx, ny;
+  double dx, dy, gamma, cfl, adv_speed;
+  const double *U;
+  unsigned long long *alpha_out;
+  DevStatus *status;
+};
+
+cudaError_t launch_alpha(const AlphaArgs &a, cudaStream_t s);
+cudaError_t launch_stage(const StageArgs &a, cudaStream_t s);
+// alpha bits -> doubles, and the CFL dt per problem
+cudaError_t launch_alpha_export(const AlphaArgs &a, const unsigned long long *bits, double *alpha,
+                                double *dt, cudaStream_t s);
+cudaError_t launch_fill(double *p, long long n, double v, cudaStream_t s);
+
+}  // namespace weno

@@ -1,0 +1,72 @@
+"""The C-ABI library loads, exports every entry point of include/weno.h, and
+its host-side argument checks work -- all without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2603_26272_gb300 import build as wbuild
+from paper_2603_26272_gb300 import weno
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    wbuild.build()
+    return weno.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "weno.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(weno_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert {"weno_rhs", "weno_step", "weno_solve", "weno_workspace_bytes"} <= set(names)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_descriptor_layout_matches_header():
+    # the header's field order and types, as ctypes lays them out (C rules)
+    assert ctypes.sizeof(weno.Desc) == 136
+    assert weno.Desc.adv_speed.offset == 128
+
+
+def test_workspace_bytes_and_argument_checks(L):
+    d = weno.make_desc(system="euler", ndim=2, nx=2048, ny=2048, bc_x="transmissive")
+    n = weno.workspace_bytes(d)
+    state = 8 * 4 * 2048 * 2048
+    assert 2 * state <= n <= 2 * state + 16384
+    assert weno.workspace_bytes(d, host=True) >= n + state
+    bad = [dict(ndim=3), dict(nx=0), dict(ndim=1, ny=2), dict(gamma=1.0), dict(cfl=0.0),
+           dict(eps=0.0), dict(precision="fp32_recon"), dict(system="advection", ndim=2, ny=4),
+           dict(nbatch=70000), dict(x1=0.0)]
+    for kw in bad:
+        args = dict(system="euler", ndim=2, nx=8, ny=8)
+        args.update(kw)
+        d = weno.make_desc(**args)
+        assert L.weno_workspace_bytes(ctypes.byref(d)) == 0, kw
+        assert L.weno_last_error().decode() != ""
+
+
+def test_entry_points_reject_bad_arguments_before_any_device_work(L):
+    d = weno.make_desc(system="euler", ndim=1, nx=16)
+    code = L.weno_rhs(ctypes.byref(d), None, None, None, 0, None)
+    assert code == weno.WENO_ERR_ARG
+    # a misaligned or too small workspace is refused
+    code = L.weno_step(ctypes.byref(d), ctypes.c_void_p(256), 0.0, None, ctypes.c_void_p(4096), 8,
+                       None)
+    assert code == weno.WENO_ERR_NOMEM
+    code = L.weno_step(ctypes.byref(d), ctypes.c_void_p(256), 0.0, None, ctypes.c_void_p(4100),
+                       1 << 30, None)
+    assert code == weno.WENO_ERR_ARG
+    assert "aligned" in L.weno_last_error().decode()
+
+
+def test_version(L):
+    assert "sm_103a" in weno.version()
