@@ -1,0 +1,99 @@
+"""Symbolic check of the rewritten formulas the CUDA kernels evaluate.
+
+The kernels (csrc/weno_device.cuh) do not evaluate the paper's formulas
+literally; they use algebraically exact rewrites chosen for FP64 economy.
+This test proves each rewrite equal to the paper's definition in exact
+arithmetic (sympy).  It does not replace the GPU parity tests: it shows the
+algebra is right, the parity tests show the code computes it.
+"""
+import sympy as sp
+
+v = sp.symbols("v0:6")
+d = [v[j + 1] - v[j] for j in range(5)]
+s = [d[k + 1] - d[k] for k in range(4)]
+
+# Section 3: printed smoothness matrices (eq. (15) for r = 3), B_2 = rev(B_0)
+B0 = sp.Matrix([[8, -19, 11], [-19, 50, -31], [11, -31, 20]]) / 6
+B1 = sp.Matrix([[8, -13, 5], [-13, 26, -13], [5, -13, 8]]) / 6
+B2 = sp.Matrix(3, 3, lambda a, b: B0[2 - a, 2 - b])
+Bd = sp.Matrix([[44, -73, 29], [-73, 122, -49], [29, -49, 20]]) / 6
+
+
+def qf(B, f):
+    f = sp.Matrix(f)
+    return sp.expand((f.T * B * f)[0])
+
+
+def test_difference_form_of_indicators():
+    t = [3 * d[1] - d[0], d[1] + d[2], 3 * d[2] - d[3], 3 * d[4] - 5 * d[3]]
+    four_beta = [sp.Rational(13, 3) * s[k] ** 2 + t[k] ** 2 for k in range(4)]
+    paper = [qf(B0, v[0:3]), qf(B1, v[1:4]), qf(B2, v[2:5]), qf(Bd, v[3:6])]
+    for k in range(4):
+        assert sp.expand(four_beta[k] - 4 * paper[k]) == 0, k
+
+
+def test_tau_as_difference_of_second_differences():
+    ctau = [-1, 5, -10, 10, -5, 1]
+    paper = sum(c * x for c, x in zip(ctau, v)) ** 2
+    r5 = (s[3] - s[0]) + 3 * (s[1] - s[2])
+    assert sp.expand(4 * r5 ** 2 - 4 * paper) == 0
+
+
+def test_candidate_fluxes_as_corrections():
+    ck = [(2, -7, 11), (-1, 5, 2), (2, 5, -1), (11, -7, 2)]
+    r = [5 * d[1] - 2 * d[0], d[1] + 2 * d[2], 4 * d[2] - d[3], 6 * d[2] - 5 * d[3] + 2 * d[4]]
+    for k in range(4):
+        paper = sum(c * v[k + m] for m, c in enumerate(ck[k])) / 6
+        assert sp.expand(v[2] + r[k] / 6 - paper) == 0, k
+
+
+def test_mean_deviation_from_differences():
+    a = [-(d[0] + d[1]), -d[1], 0, d[2], d[2] + d[3], d[2] + d[3] + d[4]]
+    for j in range(6):
+        assert sp.expand(a[j] - (v[j] - v[2])) == 0
+
+
+def test_closed_form_left_eigenvectors_2d():
+    un, ut, c, g = sp.symbols("u_n u_t c gamma", positive=True)
+    q2 = un ** 2 + ut ** 2
+    H = c ** 2 / (g - 1) + q2 / 2
+    R = sp.Matrix([[1, 1, 0, 1],
+                   [un - c, un, 0, un + c],
+                   [ut, ut, 1, ut],
+                   [H - un * c, q2 / 2, ut, H + un * c]])
+    b1 = (g - 1) / c ** 2
+    b2 = b1 * q2 / 2
+    Lk = sp.Matrix([[(b2 + un / c) / 2, -(b1 * un + 1 / c) / 2, -b1 * ut / 2, b1 / 2],
+                    [1 - b2, b1 * un, b1 * ut, -b1],
+                    [-ut, 0, 1, 0],
+                    [(b2 - un / c) / 2, -(b1 * un - 1 / c) / 2, -b1 * ut / 2, b1 / 2]])
+    assert sp.simplify(Lk * R - sp.eye(4)) == sp.zeros(4, 4)
+    # the kernel's projection with rows 2 l1, l2, l3, 2 l4
+    rho, mn, mt, E = sp.symbols("rho m_n m_t E")
+    sx = un * mn + ut * mt - E
+    z = b2 * rho - b1 * sx
+    tc = (un * rho - mn) / c
+    kern = sp.Matrix([z + tc, rho - z, mt - ut * rho, z - tc])
+    want = sp.diag(2, 1, 1, 2) * Lk * sp.Matrix([rho, mn, mt, E])
+    assert sp.simplify(kern - want) == sp.zeros(4, 1)
+    # back-projection of e = (h1/4, h2/2, h3/2, h4/4)
+    h = sp.symbols("h1:5")
+    e = [h[0] / 4, h[1] / 2, h[2] / 2, h[3] / 4]
+    S = e[0] + e[3] + e[1]
+    D = e[3] - e[0]
+    F = sp.Matrix([S, un * S + c * D, ut * S + e[2], H * (e[0] + e[3]) + un * c * D + q2 / 2 * e[1] + ut * e[2]])
+    assert sp.simplify(F - R * sp.Matrix(e)) == sp.zeros(4, 1)
+
+
+def test_closed_form_left_eigenvectors_1d():
+    u, c, g = sp.symbols("u c gamma", positive=True)
+    H = c ** 2 / (g - 1) + u ** 2 / 2
+    R = sp.Matrix([[1, 1, 1], [u - c, u, u + c], [H - u * c, u ** 2 / 2, H + u * c]])
+    b1 = (g - 1) / c ** 2
+    b2 = b1 * u ** 2 / 2
+    rho, m, E = sp.symbols("rho m E")
+    z = b2 * rho - b1 * (u * m - E)
+    tc = (u * rho - m) / c
+    kern = sp.Matrix([z + tc, rho - z, z - tc])
+    want = sp.diag(2, 1, 2) * R.inv() * sp.Matrix([rho, m, E])
+    assert sp.simplify(kern - want) == sp.zeros(3, 1)
