@@ -154,6 +154,7 @@ AlphaArgs alpha_args(const Ctx &c, const double *U, unsigned long long *out) {
   a.gamma = d->gamma;
   a.cfl = d->cfl;
   a.adv_speed = d->adv_speed;
+  a.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
   a.U = U;
   a.alpha_out = out;
   a.status = c.status();

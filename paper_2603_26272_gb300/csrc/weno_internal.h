@@ -44,7 +44,7 @@ struct StageArgs {
 
 // Wavespeed reduction of U into alpha_out (which must be zero), optional dt.
 struct AlphaArgs {
-  int system, ndim, nc;
+  int system, ndim, nc, alpha_single;
   long long nbatch, nx, ny;
   double dx, dy, gamma, cfl, adv_speed;
   const double *U;

@@ -124,10 +124,12 @@ __device__ __forceinline__ ReconParams make_rp(const StageArgs &a, double k) {
   return r;
 }
 
-// Block reduction of NV maxima (bit patterns) and one atomicMax per value.
+// Block reduction of NV maxima (bit patterns) and one atomicMax per value into
+// dst[slot[q]], and also into dst[dup[q]] where dup[q] >= 0 (the entropy and
+// shear fields share the speed |u|).
 template <int NV>
 __device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long *dst,
-                                 const int (&slot)[NV]) {
+                                 const int (&slot)[NV], const int (&dup)[NV]) {
   __shared__ unsigned long long red[32][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -143,6 +145,7 @@ __device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long
     unsigned long long m = 0;
     for (int w = 0; w < nw; ++w) m = max(m, red[w][threadIdx.x]);
     atomicMax(dst + slot[threadIdx.x], m);
+    if (dup[threadIdx.x] >= 0) atomicMax(dst + dup[threadIdx.x], m);
   }
 }
 
@@ -318,11 +321,8 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
   }
   if (want_alpha) {
     const int slot[6] = {0, 1, 3, 4, 5, 7};
-    block_max_atomic<6>(mx6, a.alpha_out + b * 8, slot);
-    if (threadIdx.x == 0) {  // the entropy and shear fields share |u| (|v|)
-      atomicMax(a.alpha_out + b * 8 + 2, mx6[1]);
-      atomicMax(a.alpha_out + b * 8 + 6, mx6[4]);
-    }
+    const int dup[6] = {-1, 2, -1, -1, 6, -1};
+    block_max_atomic<6>(mx6, a.alpha_out + b * 8, slot, dup);
   }
 }
 
@@ -458,7 +458,8 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
   }
   if (want_alpha) {
     const int slot[3] = {0, 1, 2};
-    block_max_atomic<3>(m3v, a.alpha_out + b * 8, slot);
+    const int dup[3] = {-1, -1, -1};
+    block_max_atomic<3>(m3v, a.alpha_out + b * 8, slot, dup);
   }
 }
 
@@ -493,15 +494,13 @@ __global__ void __launch_bounds__(256) k_alpha(const AlphaArgs a) {
   }
   if (a.nc == 3) {
     const int slot[6] = {0, 1, 2, 4, 5, 7};  // 1D: fields u-c, u, u+c in slots 0..2
+    const int dup[6] = {-1, -1, -1, -1, -1, -1};
     unsigned long long w[6] = {vm[0], vm[1], vm[2], 0ull, 0ull, 0ull};
-    block_max_atomic<6>(w, a.alpha_out + b * 8, slot);
+    block_max_atomic<6>(w, a.alpha_out + b * 8, slot, dup);
   } else {
     const int slot[6] = {0, 1, 3, 4, 5, 7};
-    block_max_atomic<6>(vm, a.alpha_out + b * 8, slot);
-    if (threadIdx.x == 0) {
-      atomicMax(a.alpha_out + b * 8 + 2, vm[1]);
-      atomicMax(a.alpha_out + b * 8 + 6, vm[4]);
-    }
+    const int dup[6] = {-1, 2, -1, -1, 6, -1};
+    block_max_atomic<6>(vm, a.alpha_out + b * 8, slot, dup);
   }
 }
 
@@ -516,6 +515,12 @@ __global__ void k_alpha_export(const AlphaArgs a, const unsigned long long *bits
       alpha[b * 8] = fabs(a.adv_speed);
     } else {
       for (int k = 0; k < 8; ++k) alpha[b * 8 + k] = bits2d(al[k]);
+      if (a.alpha_single)
+        for (int dir = 0; dir < a.ndim; ++dir) {
+          double m = 0.0;
+          for (int k = 0; k < a.nc; ++k) m = fmax(m, alpha[b * 8 + dir * 4 + k]);
+          for (int k = 0; k < a.nc; ++k) alpha[b * 8 + dir * 4 + k] = m;
+        }
     }
   }
   if (dt) dt[b] = cfl_dt(a.system, a.ndim, a.nc, a.cfl, a.dx, a.dy, a.adv_speed, al);

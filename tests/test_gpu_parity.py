@@ -3,7 +3,10 @@
 Tolerances (stated for the FP64 path): relative L_inf per component,
 max|gpu - oracle| / max|oracle|, at most 1e-12 for one Runge-Kutta stage (the
 right-hand side L(U), a stage state, the GLF speeds and dt) and at most 1e-10
-after a full run.  A component whose oracle values are all below 1e-14 of
+after a full run -- or, for a problem whose own conditioning is worse (the
+near-vacuum of the 123 tube turns 1e-16 input perturbations into 6e-10 in the
+oracle itself), at most 4 times the oracle's spread under a rounding-level
+perturbation of its input.  A component whose oracle values are all below 1e-14 of
 the largest component (e.g. rho v of 1D-like data) is measured against the
 largest component instead.  Both sides use FP64 throughout; they differ only
 in rounding order (the kernels use fused multiply-adds and the
@@ -48,6 +51,15 @@ def rel_err(a, b):
     return worst
 
 
+def self_sensitivity(g, U, cfl, t_final):
+    """Spread of the oracle's own full run under a +-1e-16 relative
+    perturbation of its input (the problem's rounding floor)."""
+    a, _, _ = oracle.solve(g, U, cfl, t_final)
+    rng = np.random.default_rng(1)
+    b, _, _ = oracle.solve(g, U * (1 + 1e-16 * rng.choice([-1.0, 1.0], size=U.shape)), cfl, t_final)
+    return rel_err(b, a)
+
+
 def to_gpu(U):
     return torch.from_numpy(np.ascontiguousarray(U)).cuda()
 
@@ -85,7 +97,7 @@ def cases_1d():
 
 def cases_2d():
     out = []
-    out.append(("quadrant70x45", wl.quadrant_2d(n=70, seed=3), {}))
+    out.append(("quadrant70", wl.quadrant_2d(n=70, seed=3), {}))
     q = wl.quadrant_2d(n=64, seed=4)
     q["U"] = np.ascontiguousarray(q["U"][:, :, :45, :])  # 64 x 45 (ragged in y)
     out.append(("quadrant64x45", q, {}))
@@ -171,7 +183,8 @@ def test_full_run_1d_matches_oracle(name, w, kw, _):
     t_g, n_g = weno.solve(d, Ug, w["t_final"])
     assert list(n_g) == list(n_o)
     np.testing.assert_array_equal(np.asarray(t_g), t_o)
-    assert rel_err(Ug.cpu().numpy(), U_o) <= RUN_TOL, name
+    tol = max(RUN_TOL, 4.0 * self_sensitivity(g, w["U"], d.cfl, w["t_final"]))
+    assert rel_err(Ug.cpu().numpy(), U_o) <= tol, name
     if name == "advection_T2":
         ex = w["exact"](w["x"], 2.0)
         assert np.abs(Ug.cpu().numpy()[0, 0, 0] - ex).max() < 1e-5
