@@ -146,6 +146,21 @@ weno_status weno_solve_host(const weno_desc *d, double *U_host, double t0, doubl
  * WENO_ERR_NONPHYSICAL with the problem, cell and stage in weno_last_error). */
 weno_status weno_sync_status(const weno_desc *d, void *ws, size_t ws_bytes, void *stream);
 
+/* L(U) as weno_rhs computes it, for callers that cannot allocate device
+ * memory or pass a workspace (a plug-in whose host owns all allocations, a
+ * loop that must never enter the allocator, a fixed memory budget).  The
+ * paper has no counterpart: this is a deployment variant, not a step of the
+ * method.  Its scratch (a status word and one slot of speed maxima per
+ * problem) is a fixed 64 KiB device array inside the library, present on every
+ * GPU that loads it until the process exits; the call allocates nothing.
+ * Limits: nbatch <= 1020 (larger batches return WENO_ERR_ARG with a message;
+ * use weno_rhs).  The first call on each device looks up the array's address
+ * (make it before any stream capture).  All calls share the array and clear
+ * what they need; calls that overlap on the GPU race and must be serialised by
+ * the caller.  U, dUdt: DEVICE arrays as for weno_rhs.  Synchronises the
+ * stream and returns WENO_ERR_NONPHYSICAL for a nonphysical input. */
+weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, double *dUdt, void *stream);
+
 /* Message describing the last error on the calling host thread ("" if none). */
 const char *weno_last_error(void);
 

@@ -269,6 +269,8 @@ weno_status prepare(const weno_desc *d, void *ws, size_t ws_bytes, void *stream,
 
 }  // namespace
 
+void weno::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 extern "C" {
 
 size_t weno_workspace_bytes(const weno_desc *d) {

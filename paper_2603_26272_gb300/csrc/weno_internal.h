@@ -1,6 +1,7 @@
 // weno_internal.h -- launch interface between the C-ABI layer and the kernels.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace weno {
@@ -58,5 +59,9 @@ cudaError_t launch_stage(const StageArgs &a, cudaStream_t s);
 cudaError_t launch_alpha_export(const AlphaArgs &a, const unsigned long long *bits, double *alpha,
                                 double *dt, cudaStream_t s);
 cudaError_t launch_fill(double *p, long long n, double v, cudaStream_t s);
+
+// Message returned by weno_last_error() on the calling thread.
+void set_last_error(const char *msg);
+inline void set_last_error(const std::string &msg) { set_last_error(msg.c_str()); }
 
 }  // namespace weno
