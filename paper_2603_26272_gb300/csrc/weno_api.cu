@@ -101,6 +101,7 @@ weno_status check_desc(const weno_desc *d) {
   if (!(d->cfl > 0.0) || !std::isfinite(d->cfl)) return fail(WENO_ERR_ARG, "cfl must be > 0");
   if (!(d->eps > 0.0) || !std::isfinite(d->eps)) return fail(WENO_ERR_ARG, "eps must be > 0");
   if (!(d->mu0 >= 0.0) || !std::isfinite(d->mu0)) return fail(WENO_ERR_ARG, "mu0 must be >= 0");
+  if (d->ai && !(d->mu0 > 0.0)) return fail(WENO_ERR_ARG, "mu0 must be > 0 with ai = 1 (eq. (22))");
   if (!(d->p > 0.0) || !std::isfinite(d->p)) return fail(WENO_ERR_ARG, "p must be > 0");
   if (d->ai != 0 && d->ai != 1) return fail(WENO_ERR_ARG, "ai must be 0 or 1");
   if (d->precision != WENO_PREC_FP64)

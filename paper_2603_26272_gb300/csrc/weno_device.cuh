@@ -56,6 +56,17 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 //   mu = mean |v_j - mean v| + mu_0 (eq. (22)), Gamma_k = (tau/(beta_k +
 //   eps mu^2))^p (eq. (21)), alpha_k = d_k (1 + Gamma_k) (eq. (20), L = q = 1),
 //   f = sum alpha_k f^k / sum alpha_k (eqs. (14), (19)), d = (1, 9, 9, 1)/20.
+//
+// For p = 1 the four divisions tau/b_k are removed: with b_k = 4 beta_k +
+// 4 eps mu^2, alpha_k is proportional to d_k (b_k + 4 tau) prod_{j != k} b_j.
+// Before the products, b_k and 4 tau are multiplied by the power of two that
+// brings their maximum into [1, 2) (built from the exponent bits), so the
+// products can neither overflow nor underflow; one division remains.
+//
+// mu is formed in FP32 from the FP64 differences: it enters only through
+// eps mu^2 with eps = 1e-40, which matters only for a substencil whose
+// indicator is below ~1e-30 mu^2, where a relative error of 1e-7 in mu moves
+// Gamma_k by the same relative amount and the weights by less than 1e-30.
 // ---------------------------------------------------------------------------
 template <bool AI, bool P1>
 __device__ __forceinline__ double za6(double v0, double v1, double v2, double v3, double v4,
@@ -73,34 +84,54 @@ __device__ __forceinline__ double za6(double v0, double v1, double v2, double v3
   const double Bd = fma(c13 * s3, s3, t3 * t3);
   const double B3 = 0.25 * ((B0 + B1) + (B2 + Bd));
   const double r5 = fma(3.0, s1 - s2, s3 - s0);
-  const double T = 4.0 * (r5 * r5);
+  double T = 4.0 * (r5 * r5);
   double e;
   if (AI) {
-    // deviations from the stencil mean, formed from the differences
-    const double a0 = -(d0 + d1), a1 = -d1, a3 = d2, a4 = d2 + d3, a5 = a4 + d4;
-    const double m = ((a0 + a1) + (a3 + a4) + a5) * (1.0 / 6.0);
-    const double dev = fabs(a0 - m) + fabs(a1 - m) + fabs(m) + fabs(a3 - m) + fabs(a4 - m) +
-                       fabs(a5 - m);
-    const double mu = fma(dev, 1.0 / 6.0, P.mu0s);
+    // deviations from v2, then from their mean, in FP32
+    const float f0 = __double2float_rn(d0), f1 = __double2float_rn(d1),
+                f2 = __double2float_rn(d2), f3 = __double2float_rn(d3),
+                f4 = __double2float_rn(d4);
+    const float a0 = -(f0 + f1), a1 = -f1, a3 = f2, a4 = f2 + f3, a5 = a4 + f4;
+    const float m = ((a0 + a1) + (a3 + a4) + a5) * (1.0f / 6.0f);
+    const float dev = fabsf(a0 - m) + fabsf(a1 - m) + fabsf(m) + fabsf(a3 - m) + fabsf(a4 - m) +
+                      fabsf(a5 - m);
+    const double mu = fma((double)dev, 1.0 / 6.0, P.mu0s);
     e = P.eps4 * (mu * mu);
   } else {
     e = P.efix;
   }
-  double g0 = T / (B0 + e), g1 = T / (B1 + e), g2 = T / (B2 + e), g3 = T / (B3 + e);
-  if (!P1) {
-    g0 = pow(g0, P.p);
-    g1 = pow(g1, P.p);
-    g2 = pow(g2, P.p);
-    g3 = pow(g3, P.p);
-  }
-  const double a0 = 1.0 + g0, a1 = 9.0 * (1.0 + g1), a2 = 9.0 * (1.0 + g2), a3 = 1.0 + g3;
   const double r0 = fma(5.0, d1, -2.0 * d0);
   const double r1 = fma(2.0, d2, d1);
   const double r2 = fma(4.0, d2, -d3);
   const double r3 = fma(6.0, d2, fma(-5.0, d3, 2.0 * d4));
-  const double num = fma(a0, r0, fma(a1, r1, fma(a2, r2, a3 * r3)));
-  const double den = 6.0 * ((a0 + a1) + (a2 + a3));
-  return v2 + num / den;
+  double b0 = B0 + e, b1 = B1 + e, b2 = B2 + e, b3 = B3 + e;
+  if (P1) {
+    unsigned long long mb = max(max(__double_as_longlong(b0), __double_as_longlong(b1)),
+                                max(__double_as_longlong(b2), __double_as_longlong(b3)));
+    mb = max(mb, (unsigned long long)__double_as_longlong(T));
+    const long long ex = (long long)((mb >> 52) & 0x7FF);
+    const double sc = __longlong_as_double((2046LL - ex) << 52);
+    b0 *= sc;
+    b1 *= sc;
+    b2 *= sc;
+    b3 *= sc;
+    T *= sc;
+    const double p01 = b0 * b1, p23 = b2 * b3;
+    const double a0 = (b0 + T) * (b1 * p23);
+    const double a1 = (b1 + T) * (9.0 * (b0 * p23));
+    const double a2 = (b2 + T) * (9.0 * (b3 * p01));
+    const double a3 = (b3 + T) * (b2 * p01);
+    const double num = fma(a0, r0, fma(a1, r1, fma(a2, r2, a3 * r3)));
+    const double den = 6.0 * ((a0 + a1) + (a2 + a3));
+    return v2 + num / den;
+  } else {
+    const double g0 = pow(T / b0, P.p), g1 = pow(T / b1, P.p), g2 = pow(T / b2, P.p),
+                 g3 = pow(T / b3, P.p);
+    const double a0 = 1.0 + g0, a1 = 9.0 * (1.0 + g1), a2 = 9.0 * (1.0 + g2), a3 = 1.0 + g3;
+    const double num = fma(a0, r0, fma(a1, r1, fma(a2, r2, a3 * r3)));
+    const double den = 6.0 * ((a0 + a1) + (a2 + a3));
+    return v2 + num / den;
+  }
 }
 
 // ---------------------------------------------------------------------------

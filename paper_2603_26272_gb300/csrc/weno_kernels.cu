@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
     const long long gj = ghost(j0 - 3 + r, a.ny, a.bc_y);
     const long long o = gj * a.nx + gi;
     const double rho = Ub[o], mx = Ub[plane + o], my = Ub[2 * plane + o], E = Ub[3 * plane + o];
-    const double ir = 1.0 / rho;
+    const double rs = rsqrt(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
+    const double ir = rs * rs;
     const double u = mx * ir, v = my * ir;
     const double p = gm1 * (E - 0.5 * fma(mx, u, my * v));
     if (!(pos_finite(rho) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
     pl[4 * REG + k] = u;
     pl[5 * REG + k] = v;
     pl[6 * REG + k] = rH * ir;
-    pl[7 * REG + k] = sqrt(rho);
+    pl[7 * REG + k] = rho * rs;
     pl[8 * REG + k] = mx;
     pl[9 * REG + k] = fma(mx, u, p);
     pl[10 * REG + k] = ruv;
@@ -352,7 +353,8 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
       pl[0][k] = Ub[gi];
     } else {
       const double rho = Ub[gi], m = Ub[nx + gi], E = Ub[2 * nx + gi];
-      const double ir = 1.0 / rho;
+      const double rs = rsqrt(rho);
+      const double ir = rs * rs;
       const double u = m * ir;
       const double p = gm1 * (E - 0.5 * (m * u));
       if (!(pos_finite(rho) && pos_finite(p))) record_status(a.status, 3, a.stage, b, 0, gi);
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
       pl[2][k] = E;
       pl[3][k] = u;
       pl[4][k] = rH * ir;
-      pl[5][k] = sqrt(rho);
+      pl[5][k] = rho * rs;
       pl[6][k] = m;
       pl[7][k] = fma(m, u, p);
       pl[8][k] = rH * u;

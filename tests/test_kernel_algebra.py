@@ -97,3 +97,21 @@ def test_closed_form_left_eigenvectors_1d():
     kern = sp.Matrix([z + tc, rho - z, z - tc])
     want = sp.diag(2, 1, 2) * R.inv() * sp.Matrix([rho, m, E])
     assert sp.simplify(kern - want) == sp.zeros(3, 1)
+
+
+def test_division_free_weights():
+    # omega_k = d_k (1 + T/b_k) / sum_j d_j (1 + T/b_j)
+    #         = d_k (b_k + T) prod_{j!=k} b_j / sum_j d_j (b_j + T) prod_{i!=j} b_i,
+    # and an exact common scale of b and T leaves it unchanged.
+    b = sp.symbols("b0:4", positive=True)
+    T, sc = sp.symbols("T sc", positive=True)
+    dk = [1, 9, 9, 1]
+    paper = [dk[k] * (1 + T / b[k]) for k in range(4)]
+    bs = [sc * x for x in b]
+    Ts = sc * T
+    kern = [dk[0] * (bs[0] + Ts) * (bs[1] * (bs[2] * bs[3])),
+            (bs[1] + Ts) * (9 * (bs[0] * (bs[2] * bs[3]))),
+            (bs[2] + Ts) * (9 * (bs[3] * (bs[0] * bs[1]))),
+            (bs[3] + Ts) * (bs[2] * (bs[0] * bs[1]))]
+    for k in range(4):
+        assert sp.simplify(paper[k] / sum(paper) - kern[k] / sum(kern)) == 0
