@@ -130,6 +130,38 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def precision_modes(weno, wl, torch, n=4096, steps=4, warmup=3):
+    """Configuration 4: the quadrant workload at n x n, FP64 and
+    FP32-reconstruction on the same GPU (device-timed SSP-RK3 steps)."""
+    w = wl.quadrant_2d(n=n, seed=SEED)
+    out = {"workload": "2D Euler %dx%d four-quadrant Riemann data (seed %d), SSP-RK3 CFL 0.5"
+                       % (n, n, SEED)}
+    U0 = torch.from_numpy(w["U"])
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "fp32_recon"):
+        d = weno.desc_for(w, precision=prec)
+        U = U0.cuda()
+        ws = weno.workspace(d)
+        for _ in range(warmup):
+            weno.step(d, U, ws=ws, sync=False)
+        weno.sync_status(d, ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            weno.step(d, U, ws=ws, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        weno.sync_status(d, ws)
+        ms = a.elapsed_time(b) / steps
+        out[prec] = {"value": n * n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "steps": steps, "warmup": warmup}
+        del U, ws
+        torch.cuda.empty_cache()
+    out["fp32_recon_speedup"] = out["fp32_recon"]["value"] / out["fp64"]["value"]
+    out["error_vs_fp64_oracle"] = "profiles/fp32_recon_error_512.md"
+    return out
+
+
 def cpu_baseline(seconds, window=256):
     """The oracle, as it stands, on a window of the bench workload (the
     window around the quadrant corner, as its own problem with transmissive
@@ -197,6 +229,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-modes", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -310,6 +343,11 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
+    if not args.no_precision_modes:
+        del U
+        torch.cuda.empty_cache()
+        result["precision_modes"] = precision_modes(weno, wl, torch)
+        result["gpu_launches_precision_modes"] = 4 * 2 * (4 + 3)
     if rank == 0 and not args.no_cpu_baseline:
         log("timing the CPU oracle on the host cores ...")
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

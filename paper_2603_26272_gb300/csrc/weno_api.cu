@@ -104,8 +104,11 @@ weno_status check_desc(const weno_desc *d) {
   if (d->ai && !(d->mu0 > 0.0)) return fail(WENO_ERR_ARG, "mu0 must be > 0 with ai = 1 (eq. (22))");
   if (!(d->p > 0.0) || !std::isfinite(d->p)) return fail(WENO_ERR_ARG, "p must be > 0");
   if (d->ai != 0 && d->ai != 1) return fail(WENO_ERR_ARG, "ai must be 0 or 1");
-  if (d->precision != WENO_PREC_FP64)
-    return fail(WENO_ERR_ARG, "only WENO_PREC_FP64 is available");
+  if (d->precision != WENO_PREC_FP64 && d->precision != WENO_PREC_FP32_RECON)
+    return fail(WENO_ERR_ARG, "precision must be WENO_PREC_FP64 or WENO_PREC_FP32_RECON");
+  if (d->precision == WENO_PREC_FP32_RECON && !d->ai)
+    return fail(WENO_ERR_ARG, "WENO_PREC_FP32_RECON needs ai = 1 (its normalisation relies on "
+                              "the affine-invariant weights)");
   if (d->alpha_mode != WENO_ALPHA_FIELD && d->alpha_mode != WENO_ALPHA_SINGLE)
     return fail(WENO_ERR_ARG, "alpha_mode must be WENO_ALPHA_FIELD or WENO_ALPHA_SINGLE");
   if (d->reserved != 0) return fail(WENO_ERR_ARG, "reserved must be 0");
@@ -183,6 +186,7 @@ StageArgs stage_args(const Ctx &c) {
   a.p = d->p;
   a.ai = d->ai;
   a.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
+  a.precision = d->precision;
   a.adv_speed = d->adv_speed;
   a.t_final = INFINITY;
   a.t = c.t();

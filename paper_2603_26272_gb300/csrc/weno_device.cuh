@@ -135,6 +135,96 @@ __device__ __forceinline__ double za6(double v0, double v1, double v2, double v3
 }
 
 // ---------------------------------------------------------------------------
+// FP32 reconstruction (precision mode WENO_PREC_FP32_RECON).
+//
+// Input: the five FP64 stencil differences d_j = v_{j+1} - v_j already
+// rounded to FP32.  Output: the FP32 correction c with f_hat = v2 + c.
+// The stencil is normalised by its descaler, d_j / mu with
+// mu = mean |v_j - mean v| + mu_0 (eq. (22)); with the affine-invariant
+// weights this is an exact symmetry (Gamma_k of eq. (21) is unchanged when the
+// data are scaled), so all indicators are O(1) numbers in FP32.  In normalised
+// units the sensitivity term eps mu^2 becomes eps; it is replaced by
+// eps32 = 1e-30 (1e-40 is below FP32's normal range); this changes Gamma_k
+// only for substencils flat to 1e-15 of the stencil's variation, whose rivals'
+// weights then fall to 1e-30 instead of 1e-40 -- far below FP32 resolution.
+// Weights are normalised before the products with the candidates, so no
+// intermediate can overflow.
+// ---------------------------------------------------------------------------
+struct Recon32 {
+  float eps4;   // 4 * eps32
+  float p;      // power parameter
+};
+
+template <bool P1>
+__device__ __forceinline__ float za6_f32(float e0, float e1, float e2, float e3, float e4,
+                                         const Recon32 &P) {
+  const float a0 = -(e0 + e1), a1 = -e1, a3 = e2, a4 = e2 + e3, a5 = a4 + e4;
+  const float m = ((a0 + a1) + (a3 + a4) + a5) * (1.0f / 6.0f);
+  const float dev = fabsf(a0 - m) + fabsf(a1 - m) + fabsf(m) + fabsf(a3 - m) + fabsf(a4 - m) +
+                    fabsf(a5 - m);
+  // mu_0 only guards the normalisation against 0/0; in FP32 its reciprocal
+  // would overflow, so mu is floored at 1e-30 instead (the weights do not
+  // depend on the normalisation).
+  const float mu = fmaxf(dev * (1.0f / 6.0f), 1e-30f);
+  const float im = 1.0f / mu;
+  const float d0 = e0 * im, d1 = e1 * im, d2 = e2 * im, d3 = e3 * im, d4 = e4 * im;
+  const float s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
+  const float t0 = fmaf(3.0f, d1, -d0);
+  const float t1 = d1 + d2;
+  const float t2 = fmaf(3.0f, d2, -d3);
+  const float t3 = fmaf(3.0f, d4, -5.0f * d3);
+  const float c13 = 13.0f / 3.0f;
+  const float B0 = fmaf(c13 * s0, s0, t0 * t0);
+  const float B1 = fmaf(c13 * s1, s1, t1 * t1);
+  const float B2 = fmaf(c13 * s2, s2, t2 * t2);
+  const float Bd = fmaf(c13 * s3, s3, t3 * t3);
+  const float B3 = 0.25f * ((B0 + B1) + (B2 + Bd));
+  const float r5 = fmaf(3.0f, s1 - s2, s3 - s0);
+  const float T = 4.0f * (r5 * r5);
+  float g0 = T / (B0 + P.eps4), g1 = T / (B1 + P.eps4), g2 = T / (B2 + P.eps4),
+        g3 = T / (B3 + P.eps4);
+  if (!P1) {
+    g0 = powf(g0, P.p);
+    g1 = powf(g1, P.p);
+    g2 = powf(g2, P.p);
+    g3 = powf(g3, P.p);
+  }
+  const float a0w = 1.0f + g0, a1w = 9.0f * (1.0f + g1), a2w = 9.0f * (1.0f + g2),
+              a3w = 1.0f + g3;
+  const float is = 1.0f / ((a0w + a1w) + (a2w + a3w));
+  const float r0 = fmaf(5.0f, d1, -2.0f * d0);
+  const float r1 = fmaf(2.0f, d2, d1);
+  const float r2 = fmaf(4.0f, d2, -d3);
+  const float r3 = fmaf(6.0f, d2, fmaf(-5.0f, d3, 2.0f * d4));
+  const float c = fmaf(a0w * is, r0, fmaf(a1w * is, r1, fmaf(a2w * is, r2, (a3w * is) * r3)));
+  return (c * (1.0f / 6.0f)) * mu;
+}
+
+// One characteristic field in FP32-reconstruction mode: w[j], g[j] are the
+// FP64 projections of the six stencil states and fluxes, A the field's GLF
+// speed.  Returns h = f_hat^+ + f_hat^- (kernel scaling: split without 1/2).
+// FP64 work: the ten differences, the base f+_i + f-_{i+1} and one add.
+template <bool P1>
+__device__ __forceinline__ double field_flux_f32(const double (&w)[6], const double (&g)[6],
+                                                 double A, const Recon32 &P) {
+  const float Af = (float)A;
+  float dp[5], dm[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const float dw = __double2float_rn(w[j + 1] - w[j]);
+    const float dg = __double2float_rn(g[j + 1] - g[j]);
+    dp[j] = fmaf(Af, dw, dg);
+    dm[j] = fmaf(-Af, dw, dg);
+  }
+  // f^+ on (i-2..i+3) around v2 = f^+_i; f^- mirrored (i+3..i-2) around f^-_{i+1},
+  // whose differences are -dm[4], ..., -dm[0].
+  const float cp = za6_f32<P1>(dp[0], dp[1], dp[2], dp[3], dp[4], P);
+  const float cm = za6_f32<P1>(-dm[4], -dm[3], -dm[2], -dm[1], -dm[0], P);
+  const double base = fma(A, w[2] - w[3], g[2] + g[3]);
+  return base + (double)(cp + cm);
+}
+
+// ---------------------------------------------------------------------------
 // Characteristic-wise Lax-Friedrichs flux of the Euler equations at one face
 // (Section 4.2), in the face's normal frame: components (rho, m_n, m_t, E)
 // with normal flux (F0..F3), face-normal velocity u_n, tangential u_t.

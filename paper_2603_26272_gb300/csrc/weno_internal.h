@@ -24,6 +24,7 @@ struct StageArgs {
   // scheme
   double cfl, eps, mu0, p;
   int ai, alpha_single;
+  int precision;      // 0 FP64, 1 FP32 reconstruction
   double adv_speed;
   // data
   const double *Uin;  // stage input (read with the stencil)

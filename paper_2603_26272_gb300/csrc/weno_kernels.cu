@@ -124,6 +124,13 @@ __device__ __forceinline__ ReconParams make_rp(const StageArgs &a, double k) {
   return r;
 }
 
+__device__ __forceinline__ Recon32 make_r32(const StageArgs &a) {
+  Recon32 r;
+  r.eps4 = 4.0e-30f;
+  r.p = (float)a.p;
+  return r;
+}
+
 // Block reduction of NV maxima (bit patterns) and one atomicMax per value into
 // dst[slot[q]], and also into dst[dup[q]] where dup[q] >= 0 (the entropy and
 // shear fields share the speed |u|).
@@ -154,7 +161,7 @@ __device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long
 // Shared planes per staged cell: 0 rho, 1 rho u, 2 rho v, 3 E, 4 u, 5 v, 6 H,
 // 7 sqrt(rho), 8-11 F (x flux), 12-15 G (y flux).
 // ---------------------------------------------------------------------------
-template <int TX, int TY, bool AI, bool P1>
+template <int TX, int TY, bool AI, bool P1, int PREC>
 __global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
   constexpr int W = TX + 6, HH = TY + 6, REG = W * HH;
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
@@ -245,31 +252,50 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
       const double m = fmax(fmax(A1, A2), fmax(A3, A4));
       A1 = A2 = A3 = A4 = m;
     }
-    double p1[6], p2[6], p3[6], p4[6], m1[6], m2[6], m3[6], m4[6];
+    double h1, h2, h3, h4;
+    if (PREC == 1) {
+      // FP32 reconstruction: FP64 projections, FP32 split and WENO-ZA6.
+      double W[4][6], G[4][6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const int k = base + j * stride;
-      double w1, w2, w3, w4, g1, g2, g3, g4;
-      project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], w1, w2, w3, w4);
-      project4(fs, pl[pf0 * REG + k], pl[pf1 * REG + k], pl[pf2 * REG + k], pl[pf3 * REG + k],
-               g1, g2, g3, g4);
-      p1[j] = fma(A1, w1, g1);
-      m1[j] = fma(-A1, w1, g1);
-      p2[j] = fma(A2, w2, g2);
-      m2[j] = fma(-A2, w2, g2);
-      p3[j] = fma(A3, w3, g3);
-      m3[j] = fma(-A3, w3, g3);
-      p4[j] = fma(A4, w4, g4);
-      m4[j] = fma(-A4, w4, g4);
-    }
-    const double h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
-                      za6<AI, P1>(m1[5], m1[4], m1[3], m1[2], m1[1], m1[0], rp4);
-    const double h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
-                      za6<AI, P1>(m2[5], m2[4], m2[3], m2[2], m2[1], m2[0], rp2);
-    const double h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp2) +
-                      za6<AI, P1>(m3[5], m3[4], m3[3], m3[2], m3[1], m3[0], rp2);
-    const double h4 = za6<AI, P1>(p4[0], p4[1], p4[2], p4[3], p4[4], p4[5], rp4) +
-                      za6<AI, P1>(m4[5], m4[4], m4[3], m4[2], m4[1], m4[0], rp4);
+      for (int j = 0; j < 6; ++j) {
+        const int k = base + j * stride;
+        project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], W[0][j],
+                 W[1][j], W[2][j], W[3][j]);
+        project4(fs, pl[pf0 * REG + k], pl[pf1 * REG + k], pl[pf2 * REG + k], pl[pf3 * REG + k],
+                 G[0][j], G[1][j], G[2][j], G[3][j]);
+      }
+      const Recon32 r32 = make_r32(a);
+      h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
+      h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
+      h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
+      h4 = field_flux_f32<P1>(W[3], G[3], A4, r32);
+    } else {
+      double p1[6], p2[6], p3[6], p4[6], m1[6], m2[6], m3[6], m4[6];
+  #pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int k = base + j * stride;
+        double w1, w2, w3, w4, g1, g2, g3, g4;
+        project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], w1, w2, w3, w4);
+        project4(fs, pl[pf0 * REG + k], pl[pf1 * REG + k], pl[pf2 * REG + k], pl[pf3 * REG + k],
+                 g1, g2, g3, g4);
+        p1[j] = fma(A1, w1, g1);
+        m1[j] = fma(-A1, w1, g1);
+        p2[j] = fma(A2, w2, g2);
+        m2[j] = fma(-A2, w2, g2);
+        p3[j] = fma(A3, w3, g3);
+        m3[j] = fma(-A3, w3, g3);
+        p4[j] = fma(A4, w4, g4);
+        m4[j] = fma(-A4, w4, g4);
+      }
+      h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
+                        za6<AI, P1>(m1[5], m1[4], m1[3], m1[2], m1[1], m1[0], rp4);
+      h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
+                        za6<AI, P1>(m2[5], m2[4], m2[3], m2[2], m2[1], m2[0], rp2);
+      h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp2) +
+                        za6<AI, P1>(m3[5], m3[4], m3[3], m3[2], m3[1], m3[0], rp2);
+      h4 = za6<AI, P1>(p4[0], p4[1], p4[2], p4[3], p4[4], p4[5], rp4) +
+                        za6<AI, P1>(m4[5], m4[4], m4[3], m4[2], m4[1], m4[0], rp4);
+  }
     double F0, F1, F2, F3;
     backproject4(fs, h1, h2, h3, h4, F0, F1, F2, F3);
     double *out = dir ? &fy[(fr * TX + fc) * 4] : &fx[(fr * (TX + 1) + fc) * 4];
@@ -332,7 +358,7 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
 // kT1 = 127 cells, 128 faces, one face per thread.
 // Planes: 0 rho, 1 m, 2 E, 3 u, 4 H, 5 sqrt(rho), 6-8 F  (advection: 0 u).
 // ---------------------------------------------------------------------------
-template <int NC, bool AI, bool P1>
+template <int NC, bool AI, bool P1, int PREC>
 __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
   constexpr int T = kT1, REG = T + 6;
   constexpr int NP = (NC == 3) ? 9 : 1;
@@ -377,16 +403,27 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
     if (f <= T && i0 + f - 1 < nx) {
       if (NC == 1) {
         const double A = fabs(a.adv_speed), c = a.adv_speed;
-        const ReconParams rp = make_rp(a, 2.0);
-        double pp[6], mm[6];
+        double h;
+        if (PREC == 1) {
+          double w[6], g[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const double v = pl[0][f + j];
-          pp[j] = fma(A, v, c * v);
-          mm[j] = fma(-A, v, c * v);
+          for (int j = 0; j < 6; ++j) {
+            w[j] = pl[0][f + j];
+            g[j] = c * w[j];
+          }
+          h = field_flux_f32<P1>(w, g, A, make_r32(a));
+        } else {
+          const ReconParams rp = make_rp(a, 2.0);
+          double pp[6], mm[6];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            const double v = pl[0][f + j];
+            pp[j] = fma(A, v, c * v);
+            mm[j] = fma(-A, v, c * v);
+          }
+          h = za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp) +
+              za6<AI, P1>(mm[5], mm[4], mm[3], mm[2], mm[1], mm[0], rp);
         }
-        const double h = za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp) +
-                         za6<AI, P1>(mm[5], mm[4], mm[3], mm[2], mm[1], mm[0], rp);
         fl[f][0] = 0.5 * h;
       } else {
         const int kL = f + 2, kR = f + 3;
@@ -397,27 +434,42 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
         const unsigned long long *al = a.alpha_in + b * 8;
         double A1 = bits2d(al[0]), A2 = bits2d(al[1]), A3 = bits2d(al[2]);
         if (a.alpha_single) A1 = A2 = A3 = fmax(fmax(A1, A2), A3);
-        const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
-        double p1[6], p2[6], p3[6], m1[6], m2[6], m3[6];
+        double h1, h2, h3;
+        if (PREC == 1) {
+          double W[3][6], G[3][6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const int k = f + j;
-          double w1, w2, w3, g1, g2, g3;
-          project3(fs, pl[0][k], pl[1][k], pl[2][k], w1, w2, w3);
-          project3(fs, pl[6][k], pl[7][k], pl[8][k], g1, g2, g3);
-          p1[j] = fma(A1, w1, g1);
-          m1[j] = fma(-A1, w1, g1);
-          p2[j] = fma(A2, w2, g2);
-          m2[j] = fma(-A2, w2, g2);
-          p3[j] = fma(A3, w3, g3);
-          m3[j] = fma(-A3, w3, g3);
-        }
-        const double h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
-                          za6<AI, P1>(m1[5], m1[4], m1[3], m1[2], m1[1], m1[0], rp4);
-        const double h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
-                          za6<AI, P1>(m2[5], m2[4], m2[3], m2[2], m2[1], m2[0], rp2);
-        const double h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp4) +
-                          za6<AI, P1>(m3[5], m3[4], m3[3], m3[2], m3[1], m3[0], rp4);
+          for (int j = 0; j < 6; ++j) {
+            const int k = f + j;
+            project3(fs, pl[0][k], pl[1][k], pl[2][k], W[0][j], W[1][j], W[2][j]);
+            project3(fs, pl[6][k], pl[7][k], pl[8][k], G[0][j], G[1][j], G[2][j]);
+          }
+          const Recon32 r32 = make_r32(a);
+          h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
+          h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
+          h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
+        } else {
+          const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
+          double p1[6], p2[6], p3[6], m1[6], m2[6], m3[6];
+  #pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            const int k = f + j;
+            double w1, w2, w3, g1, g2, g3;
+            project3(fs, pl[0][k], pl[1][k], pl[2][k], w1, w2, w3);
+            project3(fs, pl[6][k], pl[7][k], pl[8][k], g1, g2, g3);
+            p1[j] = fma(A1, w1, g1);
+            m1[j] = fma(-A1, w1, g1);
+            p2[j] = fma(A2, w2, g2);
+            m2[j] = fma(-A2, w2, g2);
+            p3[j] = fma(A3, w3, g3);
+            m3[j] = fma(-A3, w3, g3);
+          }
+          h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
+                            za6<AI, P1>(m1[5], m1[4], m1[3], m1[2], m1[1], m1[0], rp4);
+          h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
+                            za6<AI, P1>(m2[5], m2[4], m2[3], m2[2], m2[1], m2[0], rp2);
+          h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp4) +
+                            za6<AI, P1>(m3[5], m3[4], m3[3], m3[2], m3[1], m3[0], rp4);
+  }
         double F0, F1, F2;
         backproject3(fs, h1, h2, h3, F0, F1, F2);
         fl[f][0] = F0;
@@ -534,12 +586,12 @@ __global__ void k_fill(double *p, long long n, double v) {
     p[k] = v;
 }
 
-template <bool AI, bool P1>
+template <bool AI, bool P1, int PREC>
 cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
   if (a.ndim == 2) {
     constexpr int W = kTX + 6, HH = kTY + 6;
     const size_t smem = sizeof(double) * (16 * W * HH + 4 * ((kTX + 1) * kTY + kTX * (kTY + 1)));
-    auto kern = k_euler2d<kTX, kTY, AI, P1>;
+    auto kern = k_euler2d<kTX, kTY, AI, P1, PREC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -551,9 +603,9 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
   const long long tiles = (a.nx + kT1 - 1) / kT1;
   dim3 grid((unsigned)tiles, (unsigned)a.nbatch, 1);
   if (a.nc == 3)
-    k_line1d<3, AI, P1><<<grid, kThreads1D, 0, s>>>(a);
+    k_line1d<3, AI, P1, PREC><<<grid, kThreads1D, 0, s>>>(a);
   else
-    k_line1d<1, AI, P1><<<grid, kThreads1D, 0, s>>>(a);
+    k_line1d<1, AI, P1, PREC><<<grid, kThreads1D, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -561,8 +613,10 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
 
 cudaError_t launch_stage(const StageArgs &a, cudaStream_t s) {
   const bool p1 = (a.p == 1.0);
-  if (a.ai) return p1 ? launch_stage_t<true, true>(a, s) : launch_stage_t<true, false>(a, s);
-  return p1 ? launch_stage_t<false, true>(a, s) : launch_stage_t<false, false>(a, s);
+  if (a.precision == 1)  // FP32 reconstruction (affine-invariant weights only)
+    return p1 ? launch_stage_t<true, true, 1>(a, s) : launch_stage_t<true, false, 1>(a, s);
+  if (a.ai) return p1 ? launch_stage_t<true, true, 0>(a, s) : launch_stage_t<true, false, 0>(a, s);
+  return p1 ? launch_stage_t<false, true, 0>(a, s) : launch_stage_t<false, false, 0>(a, s);
 }
 
 cudaError_t launch_alpha(const AlphaArgs &a, cudaStream_t s) {

@@ -126,6 +126,7 @@ extern "C" weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, dou
   r.p = d->p;
   r.ai = d->ai;
   r.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
+  r.precision = d->precision;
   r.adv_speed = d->adv_speed;
   r.Uin = U;
   r.Uout = dUdt;

@@ -44,7 +44,7 @@ def test_workspace_bytes_and_argument_checks(L):
     assert 2 * state <= n <= 2 * state + 16384
     assert weno.workspace_bytes(d, host=True) >= n + state
     bad = [dict(ndim=3), dict(nx=0), dict(ndim=1, ny=2), dict(gamma=1.0), dict(cfl=0.0),
-           dict(eps=0.0), dict(precision="fp32_recon"), dict(system="advection", ndim=2, ny=4),
+           dict(eps=0.0), dict(precision="fp32_recon", ai=False), dict(system="advection", ndim=2, ny=4),
            dict(nbatch=70000), dict(x1=0.0)]
     for kw in bad:
         args = dict(system="euler", ndim=2, nx=8, ny=8)
