@@ -162,6 +162,43 @@ def precision_modes(weno, wl, torch, n=4096, steps=4, warmup=3):
     return out
 
 
+def serving(n_requests=100, seed=5):
+    """Configuration 5, scaled to about a minute: a seeded stream of mixed
+    1D/2D, FP64/FP32-reconstruction solves.  The offered Poisson rate is set
+    to 1.0x the one-at-a-time capacity (measured first on the same GPU); the
+    same arrivals are then served one at a time (weno_solve, FIFO) and by the
+    continuous-batching engine."""
+    import torch
+    from paper_2603_26272_gb300 import serve
+    sides, n1d, steps = (128, 192, 256), (256, 16384), (100, 300)
+    reqs = serve.make_requests(n_requests, seed=seed, rate=None, sides_2d=sides, n1d=n1d,
+                               steps=steps)
+    serve.serve_one_at_a_time(reqs)  # calibration: service times back to back
+    service = [r.result["done"] - r.result["admit"] for r in reqs]
+    rate = 1.0 / float(np.mean(service))
+    gaps = np.random.default_rng(seed + 1).exponential(1.0 / rate, size=len(reqs))
+    arr = np.cumsum(gaps) - gaps[0]
+    for r, a in zip(reqs, arr):
+        r.arrival = float(a)
+        r.result = {}
+    base = serve.summarize(serve.serve_one_at_a_time(reqs))
+    for r in reqs:
+        r.result = {}
+    free = torch.cuda.mem_get_info()[0]
+    eng = serve.Engine(arena_bytes=int(min(8 << 30, free // 2)), max_slots=256)
+    cont = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2))
+    eng.close()
+    return {"workload": "%d requests: 50%% 1D Euler Riemann (N log-uniform %d..%d), 50%% 2D "
+                        "quadrant (side in %s); 50%% FP64, 50%% FP32-recon; %d..%d steps each; "
+                        "Poisson arrivals (seed %d)" % (n_requests, n1d[0], n1d[1], list(sides),
+                                                        steps[0], steps[1], seed),
+            "offered_rate_per_s": rate, "offered_load_vs_one_at_a_time": 1.0,
+            "one_at_a_time": base, "continuous_batching": cont,
+            "throughput_ratio": cont["throughput_cell_updates_per_s"] / base["throughput_cell_updates_per_s"],
+            "p50_ratio": cont["p50_latency_s"] / base["p50_latency_s"],
+            "p99_ratio": cont["p99_latency_s"] / base["p99_latency_s"]}
+
+
 def cpu_baseline(seconds, window=256):
     """The oracle, as it stands, on a window of the bench workload (the
     window around the quadrant corner, as its own problem with transmissive
@@ -230,6 +267,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-modes", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=100)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -348,6 +387,9 @@ def main():
         torch.cuda.empty_cache()
         result["precision_modes"] = precision_modes(weno, wl, torch)
         result["gpu_launches_precision_modes"] = 4 * 2 * (4 + 3)
+    if not args.no_serving and rank == 0:
+        log("serving stream ...")
+        result["serving"] = serving(args.serving_requests)
     if rank == 0 and not args.no_cpu_baseline:
         log("timing the CPU oracle on the host cores ...")
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -161,6 +161,53 @@ weno_status weno_sync_status(const weno_desc *d, void *ws, size_t ws_bytes, void
  * stream and returns WENO_ERR_NONPHYSICAL for a nonphysical input. */
 weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, double *dUdt, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving engine: continuous batching of independent solves on one GPU.
+ * Each admitted problem ("slot": one Euler problem, nbatch = 1, ai = 1,
+ * p = 1, FP64 or FP32_RECON, 1D or 2D of any size) advances with its own CFL
+ * step to its own t_final; all admitted slots advance together, every engine
+ * step being one SSP-RK3 step of each unfinished slot (three launches of a
+ * persistent kernel over a device work list of all slots' tiles, replayed as
+ * one CUDA graph).  Problems can be admitted and retired between runs.  The
+ * paper has no serving layer: this is how many of its solves share a GPU.
+ *
+ * Memory: `arena` is caller-owned DEVICE memory (256-byte aligned).  Its first
+ * weno_engine_control_bytes(max_slots, max_tiles) bytes hold the engine's
+ * tables; the rest is a heap for the slots' states (weno_engine_slot_bytes
+ * each).  Admission fails with WENO_ERR_NOMEM when no slot, work-list entry
+ * or heap block is free; the engine never calls the allocator.
+ * The engine works on a CUDA stream of its own; run() is asynchronous,
+ * admit/poll/retire synchronise it.  One host thread per engine.
+ * --------------------------------------------------------------------------- */
+typedef struct weno_engine weno_engine;
+
+size_t weno_engine_control_bytes(int max_slots, int64_t max_tiles);
+/* Heap bytes one problem described by d occupies (3 states), 0 if invalid. */
+size_t weno_engine_slot_bytes(const weno_desc *d);
+/* stream: reserved, pass NULL. */
+weno_status weno_engine_create(void *arena, size_t arena_bytes, int max_slots, int64_t max_tiles,
+                               void *stream, weno_engine **out);
+/* Copy the HOST state U_host (layout of d, nbatch = 1) in, compute its speeds
+ * and give it a slot (slot_out).  t_final > 0: the problem's end time. */
+weno_status weno_engine_admit(weno_engine *e, const weno_desc *d, const double *U_host,
+                              double t_final, int *slot_out);
+/* Enqueue nsteps engine steps (asynchronous). */
+weno_status weno_engine_run(weno_engine *e, int nsteps);
+/* Wait for the enqueued steps; done[0..min(*n_done, max_done)) receives the
+ * slots that reached t_final or met a nonphysical state; n_active (may be
+ * NULL) the number of admitted slots. */
+weno_status weno_engine_poll(weno_engine *e, int *done, int max_done, int *n_done,
+                             int *n_active);
+/* Copy a slot's state to U_host (may be NULL), report its time and step
+ * count, and free the slot.  Returns WENO_ERR_NONPHYSICAL for a slot that
+ * met a nonphysical state (the other slots are unaffected). */
+weno_status weno_engine_retire(weno_engine *e, int slot, double *U_host, double *t_out,
+                               int64_t *steps_out);
+/* Free heap bytes, the largest free block and the work-list entries in use. */
+weno_status weno_engine_info(const weno_engine *e, size_t *heap_free_bytes,
+                             size_t *heap_largest, int64_t *tiles_in_use);
+weno_status weno_engine_destroy(weno_engine *e);
+
 /* Message describing the last error on the calling host thread ("" if none). */
 const char *weno_last_error(void);
 

@@ -54,6 +54,42 @@ struct AlphaArgs {
   DevStatus *status;
 };
 
+// ---------------------------------------------------------------------------
+// Serving engine: many independent solves ("slots") of mixed shape and
+// precision advanced together by one persistent kernel per Runge-Kutta stage.
+// ---------------------------------------------------------------------------
+struct SlotDev {
+  int ndim, nc, bc_x, bc_y, precision, alpha_single, active, pad;
+  long long nx, ny;
+  double dx, dy, gamma, cfl, eps, mu0, p, t_final;
+  double *U, *U1, *U2;          // state and the two stage buffers
+  unsigned long long *alpha;    // [3][8] rotating speed-maxima slots
+  double *clock;                // t, tnext, dt
+  long long *steps;
+  DevStatus *status;
+};
+
+struct EngineTile {
+  int slot;
+  int tile;
+};
+
+struct EngineArgs {
+  const SlotDev *slots;
+  const EngineTile *tiles;
+  const int *ntiles;
+  int *counters;                // [3] rotating work counters
+  int stage;                    // 1, 2, 3
+};
+
+constexpr int kEngineThreads = 256;
+constexpr int kEngine1DCells = kEngineThreads - 1;
+constexpr int kEngineTX = 32, kEngineTY = 16;
+size_t engine_smem_bytes();
+long long engine_tiles_of(int ndim, long long nx, long long ny);
+cudaError_t engine_prepare();  // kernel attributes; call before capturing
+cudaError_t launch_engine_stage(const EngineArgs &e, int grid, cudaStream_t s);
+
 cudaError_t launch_alpha(const AlphaArgs &a, cudaStream_t s);
 cudaError_t launch_stage(const StageArgs &a, cudaStream_t s);
 // alpha bits -> doubles, and the CFL dt per problem

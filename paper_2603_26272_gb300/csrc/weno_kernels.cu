@@ -69,10 +69,10 @@ __device__ double cfl_dt(int system, int ndim, int nc, double cfl, double dx, do
 // stage after next, decides this problem's dt, advances its clock.
 // Returns false if the block has nothing to do.
 __device__ bool stage_control(const StageArgs &a, long long b, bool first_block_of_b,
-                              double &dt_out) {
+                              bool zeroing_block, double &dt_out) {
   __shared__ double s_dt;
   __shared__ int s_go;
-  if (a.alpha_zero && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+  if (a.alpha_zero && zeroing_block)
     for (long long k = threadIdx.x; k < a.nbatch * 8; k += blockDim.x) a.alpha_zero[k] = 0ull;
   if (threadIdx.x == 0) {
     int go = 1;
@@ -161,21 +161,27 @@ __device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long
 // Shared planes per staged cell: 0 rho, 1 rho u, 2 rho v, 3 E, 4 u, 5 v, 6 H,
 // 7 sqrt(rho), 8-11 F (x flux), 12-15 G (y flux).
 // ---------------------------------------------------------------------------
+// One tile (tile index `tile` of problem b) of a 2D stage, run by one block.
+// sm: dynamic shared memory of smem_euler2d<TX, TY>() bytes.
+template <int TX, int TY>
+constexpr size_t smem_euler2d() {
+  return sizeof(double) * (16 * (TX + 6) * (TY + 6) + 4 * ((TX + 1) * TY + TX * (TY + 1)));
+}
+
 template <int TX, int TY, bool AI, bool P1, int PREC>
-__global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
+__device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, long long tile,
+                                             bool zeroing_block, double *sm) {
   constexpr int W = TX + 6, HH = TY + 6, REG = W * HH;
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-  extern __shared__ double sm[];
   double *const pl = sm;
   double *const fx = sm + 16 * REG;
   double *const fy = fx + NFX * 4;
 
-  const long long b = blockIdx.z;
   const long long tiles_x = (a.nx + TX - 1) / TX;
-  const long long tj = blockIdx.x / tiles_x, ti = blockIdx.x - tj * tiles_x;
+  const long long tj = tile / tiles_x, ti = tile - tj * tiles_x;
   const long long i0 = ti * TX, j0 = tj * TY;
   double dt;
-  if (!stage_control(a, b, blockIdx.x == 0, dt)) return;
+  if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
 
   const long long plane = a.nx * a.ny;
   const double *Ub = a.Uin + b * 4 * plane;
@@ -353,21 +359,28 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
   }
 }
 
+template <int TX, int TY, bool AI, bool P1, int PREC>
+__global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
+  extern __shared__ double sm[];
+  euler2d_tile<TX, TY, AI, P1, PREC>(a, blockIdx.z, blockIdx.x,
+                                     blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
+}
+
 // ---------------------------------------------------------------------------
 // 1D stage kernel: NC = 3 (Euler) or 1 (scalar advection).  Tile of
 // kT1 = 127 cells, 128 faces, one face per thread.
 // Planes: 0 rho, 1 m, 2 E, 3 u, 4 H, 5 sqrt(rho), 6-8 F  (advection: 0 u).
 // ---------------------------------------------------------------------------
-template <int NC, bool AI, bool P1, int PREC>
-__global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
-  constexpr int T = kT1, REG = T + 6;
+template <int NC, bool AI, bool P1, int PREC, int T>
+__device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, long long tile,
+                                            bool zeroing_block) {
+  constexpr int REG = T + 6;
   constexpr int NP = (NC == 3) ? 9 : 1;
   __shared__ double pl[NP][REG];
   __shared__ double fl[T + 1][NC];
-  const long long b = blockIdx.y;
-  const long long i0 = (long long)blockIdx.x * T;
+  const long long i0 = tile * T;
   double dt;
-  if (!stage_control(a, b, blockIdx.x == 0, dt)) return;
+  if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
   const long long nx = a.nx;
   const double *Ub = a.Uin + b * NC * nx;
   const double gm1 = a.gamma - 1.0;
@@ -517,6 +530,12 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
   }
 }
 
+template <int NC, bool AI, bool P1, int PREC>
+__global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
+  line1d_tile<NC, AI, P1, PREC, kT1>(a, blockIdx.y, blockIdx.x,
+                                     blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+}
+
 // ---------------------------------------------------------------------------
 // Wavespeed maxima of a state (the GLF speeds of eq. (6)), grid-stride per
 // problem (blockIdx.y).
@@ -586,11 +605,96 @@ __global__ void k_fill(double *p, long long n, double v) {
     p[k] = v;
 }
 
+
+// ---------------------------------------------------------------------------
+// Serving engine stage kernel.  A persistent grid (one 256-thread block per
+// SM) takes tiles from the device-resident work list with an atomic counter
+// (heaviest tiles first in the list) and runs the same tile functions as the
+// single-problem kernels, on the slot's own buffers, speed slots and clock.
+// The counter of the launch after next is cleared here, so consecutive
+// launches never wait on the host.  Restricted to the scheme's default
+// (Ai weights, p = 1); FP64 or FP32 reconstruction per slot.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ StageArgs slot_stage_args(const SlotDev &S, int stage) {
+  StageArgs a;
+  a.system = 1;
+  a.ndim = S.ndim;
+  a.nc = S.nc;
+  a.nbatch = 1;
+  a.nx = S.nx;
+  a.ny = S.ny;
+  a.dx = S.dx;
+  a.dy = S.dy;
+  a.bc_x = S.bc_x;
+  a.bc_y = S.bc_y;
+  a.gamma = S.gamma;
+  a.cfl = S.cfl;
+  a.eps = S.eps;
+  a.mu0 = S.mu0;
+  a.p = S.p;
+  a.ai = 1;
+  a.alpha_single = S.alpha_single;
+  a.precision = S.precision;
+  a.adv_speed = 0.0;
+  const int kin = stage - 1, kout = stage % 3, kzero = (stage + 1) % 3;
+  a.alpha_in = S.alpha + 8 * kin;
+  a.alpha_out = S.alpha + 8 * kout;
+  a.alpha_zero = S.alpha + 8 * kzero;
+  a.mode = 0;
+  a.stage = stage;
+  a.dt_fixed = 0.0;
+  a.t_final = S.t_final;
+  a.t = S.clock;
+  a.tnext = S.clock + 1;
+  a.dt = S.clock + 2;
+  a.steps = S.steps;
+  a.status = S.status;
+  if (stage == 1) {
+    a.Uin = S.U; a.Un = nullptr; a.Uout = S.U1; a.a_n = 0.0; a.a_s = 1.0;
+  } else if (stage == 2) {
+    a.Uin = S.U1; a.Un = S.U; a.Uout = S.U2; a.a_n = 0.75; a.a_s = 0.25;
+  } else {
+    a.Uin = S.U2; a.Un = S.U; a.Uout = S.U; a.a_n = 1.0 / 3.0; a.a_s = 2.0 / 3.0;
+  }
+  return a;
+}
+
+__global__ void __launch_bounds__(kEngineThreads, 1) k_engine(const EngineArgs e) {
+  extern __shared__ double sm[];
+  __shared__ int s_w;
+  const int cin = e.stage - 1, czero = (e.stage + 1) % 3;
+  if (blockIdx.x == 0 && threadIdx.x == 0) e.counters[czero] = 0;
+  const int ntiles = *e.ntiles;
+  for (;;) {
+    if (threadIdx.x == 0) s_w = atomicAdd(&e.counters[cin], 1);
+    __syncthreads();
+    const int w = s_w;
+    __syncthreads();
+    if (w >= ntiles) break;
+    const EngineTile t = e.tiles[w];
+    const SlotDev &S = e.slots[t.slot];
+    if (S.active) {
+      const StageArgs a = slot_stage_args(S, e.stage);
+      if (S.ndim == 2) {
+        if (S.precision == 1)
+          euler2d_tile<kEngineTX, kEngineTY, true, true, 1>(a, 0, t.tile, t.tile == 0, sm);
+        else
+          euler2d_tile<kEngineTX, kEngineTY, true, true, 0>(a, 0, t.tile, t.tile == 0, sm);
+      } else {
+        if (S.precision == 1)
+          line1d_tile<3, true, true, 1, kEngine1DCells>(a, 0, t.tile, t.tile == 0);
+        else
+          line1d_tile<3, true, true, 0, kEngine1DCells>(a, 0, t.tile, t.tile == 0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <bool AI, bool P1, int PREC>
 cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
   if (a.ndim == 2) {
-    constexpr int W = kTX + 6, HH = kTY + 6;
-    const size_t smem = sizeof(double) * (16 * W * HH + 4 * ((kTX + 1) * kTY + kTX * (kTY + 1)));
+    const size_t smem = smem_euler2d<kTX, kTY>();
     auto kern = k_euler2d<kTX, kTY, AI, P1, PREC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -617,6 +721,23 @@ cudaError_t launch_stage(const StageArgs &a, cudaStream_t s) {
     return p1 ? launch_stage_t<true, true, 1>(a, s) : launch_stage_t<true, false, 1>(a, s);
   if (a.ai) return p1 ? launch_stage_t<true, true, 0>(a, s) : launch_stage_t<true, false, 0>(a, s);
   return p1 ? launch_stage_t<false, true, 0>(a, s) : launch_stage_t<false, false, 0>(a, s);
+}
+
+size_t engine_smem_bytes() { return smem_euler2d<kEngineTX, kEngineTY>(); }
+
+long long engine_tiles_of(int ndim, long long nx, long long ny) {
+  if (ndim == 2) return ((nx + kEngineTX - 1) / kEngineTX) * ((ny + kEngineTY - 1) / kEngineTY);
+  return (nx + kEngine1DCells - 1) / kEngine1DCells;
+}
+
+cudaError_t engine_prepare() {
+  return cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)engine_smem_bytes());
+}
+
+cudaError_t launch_engine_stage(const EngineArgs &e, int grid, cudaStream_t s) {
+  k_engine<<<grid, kEngineThreads, engine_smem_bytes(), s>>>(e);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_alpha(const AlphaArgs &a, cudaStream_t s) {

@@ -1,0 +1,254 @@
+"""Continuous-batching serving loop over the engine of libweno.
+
+Requests are independent Euler solves (1D or 2D, FP64 or FP32
+reconstruction, each to its own final time) arriving as a Poisson stream.
+`serve_continuous` admits arrived requests whenever the engine has a free
+slot, work-list room and a free block of its device arena (admission by free
+HBM, smallest-fit bypass when the head of the queue does not fit), advances
+all admitted solves together a few engine steps at a time, and retires the
+finished ones.  `serve_one_at_a_time` is the baseline: the same requests, in
+arrival order, each solved alone with weno_solve on the same GPU.
+
+Argument marshalling and queueing only; every step of the method runs in the
+CUDA kernels of libweno.so.
+"""
+import ctypes
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import weno
+from . import workloads as wl
+
+
+class _EngineLib:
+    def __init__(self):
+        L = weno.lib()
+        P = ctypes.POINTER
+        L.weno_engine_control_bytes.restype = ctypes.c_size_t
+        L.weno_engine_control_bytes.argtypes = [ctypes.c_int, ctypes.c_int64]
+        L.weno_engine_slot_bytes.restype = ctypes.c_size_t
+        L.weno_engine_slot_bytes.argtypes = [P(weno.Desc)]
+        L.weno_engine_create.restype = ctypes.c_int
+        L.weno_engine_create.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                         ctypes.c_int64, ctypes.c_void_p, P(ctypes.c_void_p)]
+        L.weno_engine_admit.restype = ctypes.c_int
+        L.weno_engine_admit.argtypes = [ctypes.c_void_p, P(weno.Desc), ctypes.c_void_p,
+                                        ctypes.c_double, P(ctypes.c_int)]
+        L.weno_engine_run.restype = ctypes.c_int
+        L.weno_engine_run.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.weno_engine_poll.restype = ctypes.c_int
+        L.weno_engine_poll.argtypes = [ctypes.c_void_p, P(ctypes.c_int), ctypes.c_int,
+                                       P(ctypes.c_int), P(ctypes.c_int)]
+        L.weno_engine_retire.restype = ctypes.c_int
+        L.weno_engine_retire.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         P(ctypes.c_double), P(ctypes.c_int64)]
+        L.weno_engine_info.restype = ctypes.c_int
+        L.weno_engine_info.argtypes = [ctypes.c_void_p, P(ctypes.c_size_t), P(ctypes.c_size_t),
+                                       P(ctypes.c_int64)]
+        L.weno_engine_destroy.restype = ctypes.c_int
+        L.weno_engine_destroy.argtypes = [ctypes.c_void_p]
+        self.L = L
+
+
+_elib = None
+
+
+def _lib():
+    global _elib
+    if _elib is None:
+        _elib = _EngineLib()
+    return _elib.L
+
+
+class Engine:
+    """A serving engine over a device arena of `arena_bytes` (a torch tensor)."""
+
+    def __init__(self, arena_bytes, max_slots=256, max_tiles=1 << 20, device="cuda"):
+        L = _lib()
+        ctl = L.weno_engine_control_bytes(max_slots, max_tiles)
+        if arena_bytes < ctl + (1 << 20):
+            raise ValueError("arena too small for the control region (%d bytes)" % ctl)
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=device)
+        self.max_slots = max_slots
+        h = ctypes.c_void_p()
+        weno._check(L.weno_engine_create(ctypes.c_void_p(self.arena.data_ptr()),
+                                         ctypes.c_size_t(self.arena.numel()), max_slots,
+                                         max_tiles, None, ctypes.byref(h)))
+        self.h = h
+        self.shapes = {}
+
+    def slot_bytes(self, desc):
+        return _lib().weno_engine_slot_bytes(ctypes.byref(desc))
+
+    def admit(self, desc, U, t_final):
+        """U: contiguous float64 numpy array in the layout of desc.  Returns
+        the slot, or None when the engine is full (no slot, work-list room or
+        arena block)."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        slot = ctypes.c_int(-1)
+        code = _lib().weno_engine_admit(self.h, ctypes.byref(desc),
+                                        U.ctypes.data_as(ctypes.c_void_p), float(t_final),
+                                        ctypes.byref(slot))
+        if code == weno.WENO_ERR_NOMEM:
+            return None
+        weno._check(code)
+        self.shapes[slot.value] = U.shape
+        return slot.value
+
+    def run(self, nsteps):
+        weno._check(_lib().weno_engine_run(self.h, int(nsteps)))
+
+    def poll(self):
+        done = (ctypes.c_int * self.max_slots)()
+        nd, na = ctypes.c_int(0), ctypes.c_int(0)
+        weno._check(_lib().weno_engine_poll(self.h, done, self.max_slots, ctypes.byref(nd),
+                                            ctypes.byref(na)))
+        return [done[i] for i in range(min(nd.value, self.max_slots))], na.value
+
+    def retire(self, slot, want_state=True):
+        """Returns (U or None, t, steps, status code)."""
+        U = np.empty(self.shapes[slot]) if want_state else None
+        t, n = ctypes.c_double(0), ctypes.c_int64(0)
+        code = _lib().weno_engine_retire(self.h, slot,
+                                         U.ctypes.data_as(ctypes.c_void_p) if want_state else None,
+                                         ctypes.byref(t), ctypes.byref(n))
+        del self.shapes[slot]
+        if code not in (weno.WENO_OK, weno.WENO_ERR_NONPHYSICAL):
+            weno._check(code)
+        return U, t.value, n.value, code
+
+    def info(self):
+        f, lg, nt = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_int64(0)
+        weno._check(_lib().weno_engine_info(self.h, ctypes.byref(f), ctypes.byref(lg),
+                                            ctypes.byref(nt)))
+        return {"heap_free": f.value, "heap_largest": lg.value, "tiles_in_use": nt.value}
+
+    def close(self):
+        if self.h:
+            _lib().weno_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float
+    kind: str
+    precision: str
+    desc: weno.Desc
+    U: np.ndarray
+    t_final: float
+    target_steps: int
+    cells: int
+    result: dict = field(default_factory=dict)
+
+
+def make_requests(n, seed=5, rate=None, sides_2d=(128, 192, 256, 384, 512, 768, 1024),
+                  n1d=(256, 16384), steps=(100, 1000), frac_2d=0.5, frac_fp32=0.5):
+    """The serving workload: n independent solves, Poisson arrivals at `rate`
+    per second (None: all at t = 0), half 1D Euler Riemann problems with N
+    log-uniform in n1d, half 2D quadrant problems with a side from sides_2d;
+    half FP64, half FP32 reconstruction; each with a final time reached in a
+    target number of steps drawn uniformly from `steps`, converted with the
+    problem's initial CFL step (computed on the GPU by weno_wavespeeds)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n) if rate else np.zeros(n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    reqs = []
+    for k in range(n):
+        is2d = rng.random() < frac_2d
+        prec = "fp32_recon" if rng.random() < frac_fp32 else "fp64"
+        target = int(rng.integers(steps[0], steps[1] + 1))
+        sub = int(rng.integers(0, 2 ** 31))
+        if is2d:
+            side = int(sides_2d[rng.integers(0, len(sides_2d))])
+            w = wl.quadrant_2d(n=side, seed=sub)
+            cells = side * side
+        else:
+            nx = int(round(math.exp(rng.uniform(math.log(n1d[0]), math.log(n1d[1])))))
+            w = wl.riemann_batch(nbatch=1, n=nx, seed=sub)
+            cells = nx
+        d = weno.desc_for(w, precision=prec)
+        U = np.ascontiguousarray(w["U"])
+        _, dt = weno.wavespeeds(d, torch.from_numpy(U).cuda())
+        t_final = target * float(dt[0].item())
+        reqs.append(Request(k, float(arrivals[k]), "2d" if is2d else "1d", prec, d, U, t_final,
+                            target, cells))
+    return reqs
+
+
+def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, clock=time.perf_counter):
+    """Continuous batching in real time.  Fills request.result with arrival,
+    admit and completion times (seconds from the start), steps, status."""
+    pending = deque(sorted(requests, key=lambda r: r.arrival))
+    waiting = []
+    active = {}
+    t0 = clock()
+    while pending or waiting or active:
+        now = clock() - t0
+        while pending and pending[0].arrival <= now:
+            waiting.append(pending.popleft())
+        still = []
+        for r in waiting:  # FIFO; later requests may pass a head that does not fit
+            slot = engine.admit(r.desc, r.U, r.t_final)
+            if slot is None:
+                still.append(r)
+                continue
+            r.result["admit"] = clock() - t0
+            active[slot] = r
+        waiting = still
+        if active:
+            engine.run(steps_per_poll)
+            done, _ = engine.poll()
+            for slot in done:
+                U, t, n, code = engine.retire(slot, want_state=keep_states)
+                r = active.pop(slot)
+                r.result.update({"done": clock() - t0, "t": t, "steps": n, "status": code})
+                if keep_states:
+                    r.result["U"] = U
+        elif pending:
+            time.sleep(max(0.0, min(pending[0].arrival - (clock() - t0), 0.01)))
+    for r in requests:
+        r.result["arrival"] = r.arrival
+    return requests
+
+
+def serve_one_at_a_time(requests, clock=time.perf_counter):
+    """Baseline: each request solved alone (weno_solve), in arrival order."""
+    t0 = clock()
+    for r in sorted(requests, key=lambda r: r.arrival):
+        now = clock() - t0
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        U = torch.from_numpy(r.U).cuda()
+        r.result["admit"] = clock() - t0
+        try:
+            t, n = weno.solve(r.desc, U, r.t_final)
+            r.result.update({"t": t[0], "steps": n[0], "status": 0})
+        except weno.WenoError as e:
+            r.result.update({"t": float("nan"), "steps": 0, "status": e.code})
+        r.result["done"] = clock() - t0
+        r.result["arrival"] = r.arrival
+    return requests
+
+
+def summarize(requests):
+    lat = np.array([r.result["done"] - r.result["arrival"] for r in requests])
+    span = max(r.result["done"] for r in requests) - min(r.result["arrival"] for r in requests)
+    work = sum(r.cells * r.result["steps"] for r in requests)
+    return {"requests": len(requests), "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+            "makespan_s": float(span), "cell_updates": int(work),
+            "throughput_cell_updates_per_s": float(work / span) if span > 0 else None,
+            "failed": int(sum(1 for r in requests if r.result.get("status", 0) != 0))}
