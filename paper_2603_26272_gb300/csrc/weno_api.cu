@@ -13,8 +13,12 @@
 // ever waits on the host and no slot is read while it is written.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/weno.h"
@@ -210,8 +214,9 @@ weno_status reset_control(const Ctx &c, double t0) {
 
 // Launch the three stages of one SSP-RK3 step; *k is the running slot index.
 weno_status launch_step(const Ctx &c, double *U, double dt_fixed, double t_final, int *k,
-                        bool last_alpha) {
+                        bool last_alpha, int tile) {
   StageArgs a = stage_args(c);
+  a.tile_variant = tile;
   a.mode = 0;
   a.dt_fixed = dt_fixed;
   a.t_final = t_final;
@@ -255,6 +260,84 @@ weno_status read_status(const Ctx &c) {
                   where[(h.stage >= 0 && h.stage <= 4) ? h.stage : 0], h.b, h.j, h.i);
     return fail(WENO_ERR_NONPHYSICAL, buf);
   }
+  return WENO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tile autotuner for the 2D stage kernel.  The first call on a new problem
+// shape times every tile variant on the caller's data (one right-hand-side
+// stage each, written into the scratch state U1) and caches the fastest; all
+// variants compute bitwise the same result.  WENO_TILE2D=0|1|2 in the
+// environment forces a variant and skips the timing.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::tuple<long long, long long, long long, int, int, int>, int> g_tune;
+
+int tile_override() {
+  const char *v = std::getenv("WENO_TILE2D");
+  if (!v || !*v) return -1;
+  const int t = std::atoi(v);
+  return (t >= 0 && t <= 2) ? t : -1;
+}
+
+weno_status choose_tile(const Ctx &c, const double *U, const unsigned long long *alpha, int *out) {
+  *out = 0;
+  const weno_desc *d = c.d;
+  if (d->ndim != 2) return WENO_OK;
+  const int forced = tile_override();
+  if (forced >= 0) {
+    *out = forced;
+    return WENO_OK;
+  }
+  const auto key = std::make_tuple((long long)d->nx, (long long)d->ny, (long long)d->nbatch,
+                                   (int)d->precision, (int)d->ai, (int)(d->p == 1.0));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *out = it->second;
+      return WENO_OK;
+    }
+  }
+  StageArgs a = stage_args(c);
+  a.mode = 1;
+  a.stage = 4;
+  a.Uin = U;
+  a.Uout = c.u1();
+  a.alpha_in = alpha;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(WENO_ERR_CUDA, "cudaEventCreate");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(WENO_ERR_CUDA, "cudaEventCreate");
+  }
+  int best = 0;
+  float best_ms = 0.0f;
+  weno_status st = WENO_OK;
+  for (int v = 0; v < 3 && st == WENO_OK; ++v) {
+    a.tile_variant = v;
+    cudaError_t e = weno::launch_stage(a, c.s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c.s);
+    if (e == cudaSuccess) e = weno::launch_stage(a, c.s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c.s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "tile autotuner");
+      break;
+    }
+    if (v == 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WENO_OK) return st;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+  *out = best;
   return WENO_OK;
 }
 
@@ -317,7 +400,10 @@ weno_status weno_rhs(const weno_desc *d, const double *U, double *dUdt, void *ws
   if ((st = reset_control(c, 0.0)) != WENO_OK) return st;
   cudaError_t e = weno::launch_alpha(alpha_args(c, U, c.slot(0)), c.s);
   if (e != cudaSuccess) return cuda_fail(e, "alpha launch");
+  int tile = 0;
+  if ((st = choose_tile(c, U, c.slot(0), &tile)) != WENO_OK) return st;
   StageArgs a = stage_args(c);
+  a.tile_variant = tile;
   a.mode = 1;
   a.stage = 4;
   a.Uin = U;
@@ -338,8 +424,10 @@ weno_status weno_step(const weno_desc *d, double *U, double dt, double *dt_used,
   if ((st = reset_control(c, 0.0)) != WENO_OK) return st;
   cudaError_t e = weno::launch_alpha(alpha_args(c, U, c.slot(0)), c.s);
   if (e != cudaSuccess) return cuda_fail(e, "alpha launch");
+  int tile = 0;
+  if ((st = choose_tile(c, U, c.slot(0), &tile)) != WENO_OK) return st;
   int k = 0;
-  if ((st = launch_step(c, U, dt > 0.0 ? dt : 0.0, INFINITY, &k, false)) != WENO_OK) return st;
+  if ((st = launch_step(c, U, dt > 0.0 ? dt : 0.0, INFINITY, &k, false, tile)) != WENO_OK) return st;
   if (dt_used) {
     e = cudaMemcpyAsync(dt_used, c.dt(), sizeof(double) * d->nbatch, cudaMemcpyDeviceToHost, c.s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync dt");
@@ -366,13 +454,15 @@ weno_status weno_solve(const weno_desc *d, double *U, double t0, double t_final,
   // between chunks.  Launches past a problem's t_final exit at once.
   const double cells = (double)nb * d->nx * d->ny;
   const int64_t chunk = cells >= 1e6 ? 4 : (cells >= 1e5 ? 16 : 64);
+  int tile = 0;
+  if ((st = choose_tile(c, U, c.slot(0), &tile)) != WENO_OK) return st;
   int64_t n = 0;
   int k = 0;
   bool done = !(t_final > t0);
   while (!done && n < max_steps) {
     const int64_t m = (max_steps - n < chunk) ? (max_steps - n) : chunk;
     for (int64_t q = 0; q < m; ++q)
-      if ((st = launch_step(c, U, 0.0, t_final, &k, true)) != WENO_OK) return st;
+      if ((st = launch_step(c, U, 0.0, t_final, &k, true, tile)) != WENO_OK) return st;
     n += m;
     e = cudaMemcpyAsync(th.data(), c.t(), sizeof(double) * nb, cudaMemcpyDeviceToHost, c.s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync t");

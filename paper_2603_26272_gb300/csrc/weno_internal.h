@@ -25,6 +25,7 @@ struct StageArgs {
   double cfl, eps, mu0, p;
   int ai, alpha_single;
   int precision;      // 0 FP64, 1 FP32 reconstruction
+  int tile_variant;   // 2D tile shape: 0 32x16, 1 16x16, 2 16x8 (results identical)
   double adv_speed;
   // data
   const double *Uin;  // stage input (read with the stencil)

@@ -359,8 +359,8 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
   }
 }
 
-template <int TX, int TY, bool AI, bool P1, int PREC>
-__global__ void __launch_bounds__(kThreads2D, 1) k_euler2d(const StageArgs a) {
+template <int TX, int TY, int NT, bool AI, bool P1, int PREC>
+__global__ void __launch_bounds__(NT, (NT >= 256 ? 1 : 256 / NT)) k_euler2d(const StageArgs a) {
   extern __shared__ double sm[];
   euler2d_tile<TX, TY, AI, P1, PREC>(a, blockIdx.z, blockIdx.x,
                                      blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
@@ -691,18 +691,26 @@ __global__ void __launch_bounds__(kEngineThreads, 1) k_engine(const EngineArgs e
   }
 }
 
+template <int TX, int TY, int NT, bool AI, bool P1, int PREC>
+cudaError_t launch_2d(const StageArgs &a, cudaStream_t s) {
+  const size_t smem = smem_euler2d<TX, TY>();
+  auto kern = k_euler2d<TX, TY, NT, AI, P1, PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = ((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
+  dim3 grid((unsigned)tiles, 1, (unsigned)a.nbatch);
+  kern<<<grid, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <bool AI, bool P1, int PREC>
 cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
   if (a.ndim == 2) {
-    const size_t smem = smem_euler2d<kTX, kTY>();
-    auto kern = k_euler2d<kTX, kTY, AI, P1, PREC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    const long long tiles = ((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY);
-    dim3 grid((unsigned)tiles, 1, (unsigned)a.nbatch);
-    kern<<<grid, kThreads2D, smem, s>>>(a);
-    return cudaGetLastError();
+    // tile variants: 0 = 32x16 cells / 256 threads (fewest halo faces),
+    // 1 = 16x16 / 128, 2 = 16x8 / 64 (more tiles for small grids)
+    if (a.tile_variant == 1) return launch_2d<16, 16, 128, AI, P1, PREC>(a, s);
+    if (a.tile_variant == 2) return launch_2d<16, 8, 64, AI, P1, PREC>(a, s);
+    return launch_2d<kTX, kTY, kThreads2D, AI, P1, PREC>(a, s);
   }
   const long long tiles = (a.nx + kT1 - 1) / kT1;
   dim3 grid((unsigned)tiles, (unsigned)a.nbatch, 1);
