@@ -162,6 +162,11 @@ def precision_modes(weno, wl, torch, n=4096, steps=4, warmup=3):
     return out
 
 
+# admission budget of the engine: admitted solves' cost per step, in 2D FP64
+# cells (about 2 tiles per SM of 16x16 cells on 152 SMs, with a margin).
+WORK_BUDGET = 250e3
+
+
 def serving(n_requests=100, seed=5):
     """Configuration 5, scaled to about a minute: a seeded stream of mixed
     1D/2D, FP64/FP32-reconstruction solves.  The offered Poisson rate is set
@@ -175,6 +180,7 @@ def serving(n_requests=100, seed=5):
                                steps=steps)
     serve.serve_one_at_a_time(reqs)  # calibration: service times back to back
     service = [r.result["done"] - r.result["admit"] for r in reqs]
+    calib_thr = serve.summarize(reqs)["throughput_cell_updates_per_s"]
     rate = 1.0 / float(np.mean(service))
     gaps = np.random.default_rng(seed + 1).exponential(1.0 / rate, size=len(reqs))
     arr = np.cumsum(gaps) - gaps[0]
@@ -186,7 +192,15 @@ def serving(n_requests=100, seed=5):
         r.result = {}
     free = torch.cuda.mem_get_info()[0]
     eng = serve.Engine(arena_bytes=int(min(8 << 30, free // 2)), max_slots=256)
-    cont = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2))
+    cont = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2,
+                                                  work_budget=WORK_BUDGET))
+    # capacity: every request present at t = 0, engine versus the back-to-back
+    # one-at-a-time calibration run above
+    for r in reqs:
+        r.arrival = 0.0
+        r.result = {}
+    sat = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2,
+                                                 work_budget=WORK_BUDGET))
     eng.close()
     return {"workload": "%d requests: 50%% 1D Euler Riemann (N log-uniform %d..%d), 50%% 2D "
                         "quadrant (side in %s); 50%% FP64, 50%% FP32-recon; %d..%d steps each; "
@@ -196,7 +210,11 @@ def serving(n_requests=100, seed=5):
             "one_at_a_time": base, "continuous_batching": cont,
             "throughput_ratio": cont["throughput_cell_updates_per_s"] / base["throughput_cell_updates_per_s"],
             "p50_ratio": cont["p50_latency_s"] / base["p50_latency_s"],
-            "p99_ratio": cont["p99_latency_s"] / base["p99_latency_s"]}
+            "p99_ratio": cont["p99_latency_s"] / base["p99_latency_s"],
+            "work_budget_cell_units": WORK_BUDGET,
+            "capacity_one_at_a_time_cell_updates_per_s": calib_thr,
+            "capacity_continuous_cell_updates_per_s": sat["throughput_cell_updates_per_s"],
+            "capacity_ratio": sat["throughput_cell_updates_per_s"] / calib_thr}
 
 
 def cpu_baseline(seconds, window=256):

@@ -241,7 +241,7 @@ weno_status weno_engine_create(void *arena, size_t arena_bytes, int max_slots, i
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  E->grid = sms > 0 ? sms : 1;
+  E->grid = (sms > 0 ? sms : 1) * weno::kEngineBlocksPerSM;
   e = cudaMemsetAsync(arena, 0, L.total, E->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(E->s);
   if (e != cudaSuccess) {

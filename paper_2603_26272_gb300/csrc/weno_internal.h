@@ -83,9 +83,10 @@ struct EngineArgs {
   int stage;                    // 1, 2, 3
 };
 
-constexpr int kEngineThreads = 256;
+constexpr int kEngineThreads = 128;
+constexpr int kEngineBlocksPerSM = 2;
 constexpr int kEngine1DCells = kEngineThreads - 1;
-constexpr int kEngineTX = 32, kEngineTY = 16;
+constexpr int kEngineTX = 16, kEngineTY = 16;
 size_t engine_smem_bytes();
 long long engine_tiles_of(int ndim, long long nx, long long ny);
 cudaError_t engine_prepare();  // kernel attributes; call before capturing

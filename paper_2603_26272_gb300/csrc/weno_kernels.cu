@@ -371,13 +371,20 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 1 : 256 / NT)) k_euler2d(cons
 // kT1 = 127 cells, 128 faces, one face per thread.
 // Planes: 0 rho, 1 m, 2 E, 3 u, 4 H, 5 sqrt(rho), 6-8 F  (advection: 0 u).
 // ---------------------------------------------------------------------------
+template <int NC, int T>
+constexpr size_t smem_line1d() {
+  return sizeof(double) * (((NC == 3) ? 9 : 1) * (T + 6) + (T + 1) * NC);
+}
+
+// One tile of T cells (T + 1 faces, one per thread; blockDim = T + 1) of a
+// 1D stage.  sm: dynamic shared memory of smem_line1d<NC, T>() bytes.
 template <int NC, bool AI, bool P1, int PREC, int T>
 __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, long long tile,
-                                            bool zeroing_block) {
+                                            bool zeroing_block, double *sm) {
   constexpr int REG = T + 6;
   constexpr int NP = (NC == 3) ? 9 : 1;
-  __shared__ double pl[NP][REG];
-  __shared__ double fl[T + 1][NC];
+  double(*pl)[REG] = reinterpret_cast<double(*)[REG]>(sm);
+  double(*fl)[NC] = reinterpret_cast<double(*)[NC]>(sm + NP * REG);
   const long long i0 = tile * T;
   double dt;
   if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
@@ -532,8 +539,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
 
 template <int NC, bool AI, bool P1, int PREC>
 __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
+  extern __shared__ double sm[];
   line1d_tile<NC, AI, P1, PREC, kT1>(a, blockIdx.y, blockIdx.x,
-                                     blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+                                     blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -659,7 +667,7 @@ __device__ __forceinline__ StageArgs slot_stage_args(const SlotDev &S, int stage
   return a;
 }
 
-__global__ void __launch_bounds__(kEngineThreads, 1) k_engine(const EngineArgs e) {
+__global__ void __launch_bounds__(kEngineThreads, kEngineBlocksPerSM) k_engine(const EngineArgs e) {
   extern __shared__ double sm[];
   __shared__ int s_w;
   const int cin = e.stage - 1, czero = (e.stage + 1) % 3;
@@ -682,9 +690,9 @@ __global__ void __launch_bounds__(kEngineThreads, 1) k_engine(const EngineArgs e
           euler2d_tile<kEngineTX, kEngineTY, true, true, 0>(a, 0, t.tile, t.tile == 0, sm);
       } else {
         if (S.precision == 1)
-          line1d_tile<3, true, true, 1, kEngine1DCells>(a, 0, t.tile, t.tile == 0);
+          line1d_tile<3, true, true, 1, kEngine1DCells>(a, 0, t.tile, t.tile == 0, sm);
         else
-          line1d_tile<3, true, true, 0, kEngine1DCells>(a, 0, t.tile, t.tile == 0);
+          line1d_tile<3, true, true, 0, kEngine1DCells>(a, 0, t.tile, t.tile == 0, sm);
       }
     }
     __syncthreads();
@@ -715,9 +723,9 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
   const long long tiles = (a.nx + kT1 - 1) / kT1;
   dim3 grid((unsigned)tiles, (unsigned)a.nbatch, 1);
   if (a.nc == 3)
-    k_line1d<3, AI, P1, PREC><<<grid, kThreads1D, 0, s>>>(a);
+    k_line1d<3, AI, P1, PREC><<<grid, kThreads1D, smem_line1d<3, kT1>(), s>>>(a);
   else
-    k_line1d<1, AI, P1, PREC><<<grid, kThreads1D, 0, s>>>(a);
+    k_line1d<1, AI, P1, PREC><<<grid, kThreads1D, smem_line1d<1, kT1>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -731,7 +739,10 @@ cudaError_t launch_stage(const StageArgs &a, cudaStream_t s) {
   return p1 ? launch_stage_t<false, true, 0>(a, s) : launch_stage_t<false, false, 0>(a, s);
 }
 
-size_t engine_smem_bytes() { return smem_euler2d<kEngineTX, kEngineTY>(); }
+size_t engine_smem_bytes() {
+  const size_t a = smem_euler2d<kEngineTX, kEngineTY>(), b = smem_line1d<3, kEngine1DCells>();
+  return a > b ? a : b;
+}
 
 long long engine_tiles_of(int ndim, long long nx, long long ny) {
   if (ndim == 2) return ((nx + kEngineTX - 1) / kEngineTX) * ((ny + kEngineTY - 1) / kEngineTY);

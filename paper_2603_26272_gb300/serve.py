@@ -188,25 +188,50 @@ def make_requests(n, seed=5, rate=None, sides_2d=(128, 192, 256, 384, 512, 768, 
     return reqs
 
 
-def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, clock=time.perf_counter):
+# Relative cost of one cell-step by class (2D FP64 = 1), from the measured
+# full-GPU rates of the stage kernels: 2D FP32-recon 2.9x faster; a 1D cell has
+# one interface of three fields instead of two of four.
+COST = {("2d", "fp64"): 1.0, ("2d", "fp32_recon"): 0.35, ("1d", "fp64"): 0.4,
+        ("1d", "fp32_recon"): 0.15}
+
+
+def work_units(r):
+    return r.cells * COST.get((getattr(r, "kind", "2d"), getattr(r, "precision", "fp64")), 1.0)
+
+
+def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, work_budget=None,
+                     clock=time.perf_counter):
     """Continuous batching in real time.  Fills request.result with arrival,
-    admit and completion times (seconds from the start), steps, status."""
+    admit and completion times (seconds from the start), steps, status.
+
+    Admission is first-come first-served under two limits: the engine must
+    have room (slot, work list, arena block -- admission by free HBM; a
+    request that does not fit lets later, smaller ones pass) and, when
+    `work_budget` is set, the admitted solves' cost per step (work_units)
+    must stay within it, so the GPU is kept full without stretching every
+    solve by sharing it with all others."""
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     waiting = []
     active = {}
+    load = 0.0
     t0 = clock()
     while pending or waiting or active:
         now = clock() - t0
         while pending and pending[0].arrival <= now:
             waiting.append(pending.popleft())
         still = []
-        for r in waiting:  # FIFO; later requests may pass a head that does not fit
+        for i, r in enumerate(waiting):
+            wu = work_units(r)
+            if work_budget is not None and active and load + wu > work_budget:
+                still.extend(waiting[i:])  # keep arrival order behind the budget
+                break
             slot = engine.admit(r.desc, r.U, r.t_final)
             if slot is None:
                 still.append(r)
                 continue
             r.result["admit"] = clock() - t0
             active[slot] = r
+            load += wu
         waiting = still
         if active:
             engine.run(steps_per_poll)
@@ -214,6 +239,7 @@ def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, cloc
             for slot in done:
                 U, t, n, code = engine.retire(slot, want_state=keep_states)
                 r = active.pop(slot)
+                load -= work_units(r)
                 r.result.update({"done": clock() - t0, "t": t, "steps": n, "status": code})
                 if keep_states:
                     r.result["U"] = U
