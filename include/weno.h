@@ -11,7 +11,7 @@
  * ---------------------------------------
  * State layout: U is a contiguous array of doubles [nbatch][ncomp][ny][nx],
  *   x fastest, holding nbatch independent problems of the same shape.
- *   ncomp = 1 for scalar advection (u), 3 for 1D Euler (rho, rho u, E),
+ *   ncomp = 1 for the scalar equations (u), 3 for 1D Euler (rho, rho u, E),
  *   4 for 2D Euler (rho, rho u, rho v, E); ny = 1 in 1D.  Cells are uniform:
  *   dx = (x1 - x0) / nx, dy = (y1 - y0) / ny (Section 2: x_{i+1/2} = a + i dx).
  * Memory: every array argument named U, dUdt, alpha or ws is DEVICE memory
@@ -50,7 +50,12 @@ typedef enum {
   WENO_ERR_MAXSTEPS = 6     /* weno_solve stopped at max_steps before t_final */
 } weno_status;
 
-enum { WENO_SYS_ADVECTION = 0, WENO_SYS_EULER = 1 };
+enum {
+  WENO_SYS_ADVECTION = 0,       /* u_t + a u_x = 0                                    */
+  WENO_SYS_EULER = 1,           /* Euler equations, gamma-law gas (Section 4.2, 4.3)  */
+  WENO_SYS_BURGERS = 2,         /* u_t + (u^2/2)_x = 0 (Section 4.1, Table 5)         */
+  WENO_SYS_BUCKLEY_LEVERETT = 3 /* u_t + (u^2/(u^2 + (1-u)^2/4))_x = 0 (Table 5)      */
+};
 enum { WENO_BC_TRANSMISSIVE = 0, WENO_BC_PERIODIC = 1 };
 enum { WENO_PREC_FP64 = 0, WENO_PREC_FP32_RECON = 1 };
 enum { WENO_ALPHA_FIELD = 0, WENO_ALPHA_SINGLE = 1 };
@@ -59,7 +64,7 @@ enum { WENO_ALPHA_FIELD = 0, WENO_ALPHA_SINGLE = 1 };
  * preamble), mu0 = 1e-40 (eq. (22)), p = 1 (Section 4 preamble; L = q = 1
  * are fixed, Section 2.1 after Table 1), gamma = 1.4 (Section 4.2). */
 typedef struct weno_desc {
-  int32_t system;     /* WENO_SYS_ADVECTION (u_t + a u_x = 0) or WENO_SYS_EULER   */
+  int32_t system;     /* WENO_SYS_*; the scalar equations are 1D                  */
   int32_t ndim;       /* 1 or 2 (advection: 1)                                    */
   int64_t nbatch;     /* number of independent problems, >= 1                     */
   int64_t nx, ny;     /* cells per axis, nx >= 1, ny >= 1 (ny = 1 when ndim = 1)  */
@@ -88,7 +93,9 @@ size_t weno_workspace_bytes(const weno_desc *d);
  * alpha[b*8 + dir*4 + m] = max over all cells of problem b of |lambda_m|
  * (dir 0 = x, 1 = y; m = characteristic field in the order u-c, u, u(, u+c);
  * unused slots 0), and the CFL time step dt[b] (1D: cfl dx / max(|u|+c);
- * 2D: cfl / (max(|u|+c)/dx + max(|v|+c)/dy); advection: cfl dx / |a|).
+ * 2D: cfl / (max(|u|+c)/dx + max(|v|+c)/dy); scalar: cfl dx / alpha).
+ * For a scalar flux alpha[b*8] = max |f'(u)| over the range [min u, max u]
+ * of the data (for Buckley-Leverett f' peaks inside that range).
  * alpha and dt are DEVICE arrays of nbatch*8 and nbatch doubles.
  * Asynchronous. */
 weno_status weno_wavespeeds(const weno_desc *d, const double *U, double *alpha, double *dt,

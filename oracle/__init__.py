@@ -92,7 +92,7 @@ def make_grid(system="euler", ndim=1, nbatch=1, nx=1, ny=1, dx=1.0, dy=1.0, bc_x
               alpha_mode="field", adv_speed=1.0):
     bcs = {"transmissive": 0, "periodic": 1}
     g = OraGrid()
-    g.system = {"advection": 0, "euler": 1}[system]
+    g.system = {"advection": 0, "euler": 1, "burgers": 2, "buckley_leverett": 3}[system]
     g.ndim = ndim
     g.nbatch = nbatch
     g.nx = nx
@@ -112,7 +112,7 @@ def make_grid(system="euler", ndim=1, nbatch=1, nx=1, ny=1, dx=1.0, dy=1.0, bc_x
 
 
 def ncomp(g):
-    if g.system == 0:
+    if g.system != 1:
         return 1
     return 3 if g.ndim == 1 else 4
 

@@ -314,8 +314,57 @@ bool invert(int n, const double A_in[4][4], double Ainv[4][4]) {
 }
 
 int ncomp_of(const ora_grid *g) {
-  if (g->system == 0) return 1;
+  if (g->system != 1) return 1;
   return g->ndim == 1 ? 3 : 4;
+}
+
+// Scalar fluxes of Section 4.1: linear advection f = a u; Burgers f = u^2/2
+// (convex); Buckley-Leverett f = u^2 / (u^2 + 0.25 (1-u)^2) (nonconvex,
+// Table 5).  f' is their derivative.
+double scalar_flux(const ora_grid *g, double u) {
+  if (g->system == 2) return 0.5 * u * u;
+  if (g->system == 3) return u * u / (u * u + 0.25 * (1.0 - u) * (1.0 - u));
+  return g->adv_speed * u;
+}
+
+double scalar_dflux(const ora_grid *g, double u) {
+  if (g->system == 2) return u;
+  if (g->system == 3) {
+    const double D = u * u + 0.25 * (1.0 - u) * (1.0 - u);
+    return 0.5 * u * (1.0 - u) / (D * D);
+  }
+  return g->adv_speed;
+}
+
+// Maximiser of the Buckley-Leverett f' on [0, 1] (f' >= 0 there, zero at both
+// ends and unimodal), by golden-section search.
+double bl_speed_argmax() {
+  ora_grid g;
+  std::memset(&g, 0, sizeof(g));
+  g.system = 3;
+  const double r = 0.5 * (std::sqrt(5.0) - 1.0);
+  double a = 0.0, b = 1.0;
+  for (int it = 0; it < 200 && b - a > 1e-15; ++it) {
+    const double c = b - r * (b - a), d = a + r * (b - a);
+    if (scalar_dflux(&g, c) > scalar_dflux(&g, d))
+      b = d;
+    else
+      a = c;
+  }
+  return 0.5 * (a + b);
+}
+
+// Eq. (6) for a scalar flux: alpha = max |f'(Q)| over the states Q between the
+// smallest and largest value of the data (reading: for a nonconvex flux the
+// largest speed of a Riemann fan lies inside that range, not at a cell state;
+// for a convex or linear flux this is the maximum over the cells).
+double scalar_alpha(const ora_grid *g, double umin, double umax) {
+  double a = std::fmax(std::fabs(scalar_dflux(g, umin)), std::fabs(scalar_dflux(g, umax)));
+  if (g->system == 3) {
+    const double us = bl_speed_argmax();
+    if (umin <= us && us <= umax) a = std::fmax(a, std::fabs(scalar_dflux(g, us)));
+  }
+  return a;
 }
 
 // Ghost-cell index map (3 ghosts per side for the 6-point stencil):
@@ -338,10 +387,10 @@ int64_t ghost(int64_t k, int64_t n, int bc) {
 int face_flux(const ora_grid *g, int dir, const double st[6][4], const double *alpha,
               double *Fhat) {
   const int nc = ncomp_of(g);
-  if (g->system == 0) {
+  if (g->system != 1) {
     double fp[6], fm[6];
     for (int j = 0; j < 6; ++j) {
-      double f = g->adv_speed * st[j][0];
+      double f = scalar_flux(g, st[j][0]);
       fp[j] = 0.5 * (f + alpha[0] * st[j][0]);
       fm[5 - j] = 0.5 * (f - alpha[0] * st[j][0]);
     }
@@ -408,8 +457,8 @@ int check_grid(const ora_grid *g) {
   if (!g || g->nbatch < 1 || g->nx < 1 || g->ny < 1) return 1;
   if (g->ndim != 1 && g->ndim != 2) return 1;
   if (g->ndim == 1 && g->ny != 1) return 1;
-  if (g->system != 0 && g->system != 1) return 1;
-  if (g->system == 0 && g->ndim != 1) return 1;
+  if (g->system < 0 || g->system > 3) return 1;
+  if (g->system != 1 && g->ndim != 1) return 1;
   return 0;
 }
 
@@ -545,6 +594,16 @@ int ora_alpha(const ora_grid *g, const double *U, double *alpha) {
       continue;
     }
     const double *Ub = U + b * nc * plane;
+    if (g->system != 1) {
+      double umin = Ub[0], umax = Ub[0];
+      for (int64_t c = 0; c < plane; ++c) {
+        if (!std::isfinite(Ub[c])) return 2;
+        umin = std::fmin(umin, Ub[c]);
+        umax = std::fmax(umax, Ub[c]);
+      }
+      al[0] = scalar_alpha(g, umin, umax);
+      continue;
+    }
     for (int64_t c = 0; c < plane; ++c) {
       double s[4];
       for (int k = 0; k < nc; ++k) s[k] = Ub[k * plane + c];
@@ -625,6 +684,15 @@ int ora_cfl_dt(const ora_grid *g, const double *U, double cfl, double *dt) {
       continue;
     }
     const double *Ub = U + b * nc * plane;
+    if (g->system != 1) {
+      double umin = Ub[0], umax = Ub[0];
+      for (int64_t c = 0; c < plane; ++c) {
+        umin = std::fmin(umin, Ub[c]);
+        umax = std::fmax(umax, Ub[c]);
+      }
+      dt[b] = cfl * g->dx / scalar_alpha(g, umin, umax);
+      continue;
+    }
     double sx = 0, sy = 0;
     for (int64_t c = 0; c < plane; ++c) {
       double s[4];

@@ -12,7 +12,7 @@
  * sixth-order scheme (WENO-ZA6) and Section 4 the Euler experiments.
  *
  * Layout of every state array: [nbatch][ncomp][ny][nx], contiguous doubles,
- * x fastest.  ncomp = 1 (scalar advection), 3 (1D Euler: rho, rho*u, E) or
+ * x fastest.  ncomp = 1 (scalar equations), 3 (1D Euler: rho, rho*u, E) or
  * 4 (2D Euler: rho, rho*u, rho*v, E).  ny = 1 in 1D.
  *
  * Return codes: 0 = ok, 1 = bad argument, 2 = nonphysical state met
@@ -28,7 +28,8 @@ extern "C" {
 
 /* The oracle's own description of a problem (not the CUDA library's). */
 typedef struct {
-  int32_t system;   /* 0 = scalar advection u_t + a u_x = 0, 1 = Euler           */
+  int32_t system;   /* 0 = advection u_t + a u_x = 0, 1 = Euler, 2 = Burgers,    */
+                    /* 3 = Buckley-Leverett (scalar systems are 1D)             */
   int32_t ndim;     /* 1 or 2                                                   */
   int64_t nbatch;   /* independent problems of the same shape                   */
   int64_t nx, ny;   /* cells per axis (ny = 1 in 1D)                            */

@@ -44,7 +44,7 @@ weno_status cuda_fail(cudaError_t e, const char *what) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int ncomp(const weno_desc *d) {
-  if (d->system == WENO_SYS_ADVECTION) return 1;
+  if (d->system != WENO_SYS_EULER) return 1;
   return d->ndim == 1 ? 3 : 4;
 }
 
@@ -83,11 +83,11 @@ Layout layout(const weno_desc *d) {
 
 weno_status check_desc(const weno_desc *d) {
   if (!d) return fail(WENO_ERR_ARG, "descriptor is NULL");
-  if (d->system != WENO_SYS_ADVECTION && d->system != WENO_SYS_EULER)
-    return fail(WENO_ERR_ARG, "system must be WENO_SYS_ADVECTION or WENO_SYS_EULER");
+  if (d->system < WENO_SYS_ADVECTION || d->system > WENO_SYS_BUCKLEY_LEVERETT)
+    return fail(WENO_ERR_ARG, "system must be one of WENO_SYS_*");
   if (d->ndim != 1 && d->ndim != 2) return fail(WENO_ERR_ARG, "ndim must be 1 or 2");
-  if (d->system == WENO_SYS_ADVECTION && d->ndim != 1)
-    return fail(WENO_ERR_ARG, "advection is one-dimensional");
+  if (d->system != WENO_SYS_EULER && d->ndim != 1)
+    return fail(WENO_ERR_ARG, "the scalar equations are one-dimensional");
   if (d->nbatch < 1 || d->nbatch > 65535) return fail(WENO_ERR_ARG, "nbatch must be in [1, 65535]");
   if (d->nx < 1 || d->ny < 1) return fail(WENO_ERR_ARG, "nx and ny must be >= 1");
   if (d->ndim == 1 && d->ny != 1) return fail(WENO_ERR_ARG, "ny must be 1 in 1D");
@@ -162,6 +162,7 @@ AlphaArgs alpha_args(const Ctx &c, const double *U, unsigned long long *out) {
   a.gamma = d->gamma;
   a.cfl = d->cfl;
   a.adv_speed = d->adv_speed;
+  a.ustar = weno::bl_speed_argmax();
   a.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
   a.U = U;
   a.alpha_out = out;
@@ -191,6 +192,7 @@ StageArgs stage_args(const Ctx &c) {
   a.ai = d->ai;
   a.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
   a.precision = d->precision;
+  a.ustar = weno::bl_speed_argmax();
   a.adv_speed = d->adv_speed;
   a.t_final = INFINITY;
   a.t = c.t();
@@ -358,6 +360,28 @@ weno_status prepare(const weno_desc *d, void *ws, size_t ws_bytes, void *stream,
 }  // namespace
 
 void weno::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+// Where the Buckley-Leverett speed f'(u) = u(1-u) / (2 D^2), D = u^2 +
+// (1-u)^2 / 4, peaks on [0, 1]: the root of its derivative, i.e. of
+// (1 - 2u) D = 2 u (1 - u) D', D' = 2u - (1 - u)/2, found by bisection (the
+// left side minus the right side changes sign once on (0, 1)).
+double weno::bl_speed_argmax() {
+  auto h = [](double u) {
+    const double D = u * u + 0.25 * (1.0 - u) * (1.0 - u);
+    const double Dp = 2.0 * u - 0.5 * (1.0 - u);
+    return (1.0 - 2.0 * u) * D - 2.0 * u * (1.0 - u) * Dp;
+  };
+  double lo = 0.0, hi = 1.0;  // h(0) = 0.25 > 0, h(1) = -1 < 0
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (h(mid) > 0.0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
 
 extern "C" {
 

@@ -36,6 +36,49 @@ __device__ __forceinline__ bool pos_finite(double x) {
   return b > 0 && b < 0x7FF0000000000000LL;
 }
 
+// Order-preserving map of any double to an unsigned integer (and back), so
+// signed minima and maxima can be reduced with integer atomicMax.
+__device__ __forceinline__ unsigned long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? ((unsigned long long)b | 0x8000000000000000ull) : ~(unsigned long long)b;
+}
+__device__ __forceinline__ double okey_inv(unsigned long long k) {
+  return __longlong_as_double((k & 0x8000000000000000ull) ? (long long)(k & 0x7FFFFFFFFFFFFFFFull)
+                                                           : (long long)~k);
+}
+
+// Scalar fluxes (Section 4.1): system 0 linear advection f = a u, 2 Burgers
+// f = u^2/2, 3 Buckley-Leverett f = u^2 / (u^2 + 0.25 (1-u)^2); f' below.
+__device__ __forceinline__ double scalar_flux(int system, double a, double u) {
+  if (system == 2) return 0.5 * (u * u);
+  if (system == 3) {
+    const double q = 1.0 - u;
+    const double uu = u * u;
+    return uu / fma(0.25 * q, q, uu);
+  }
+  return a * u;
+}
+__device__ __forceinline__ double scalar_speed(int system, double a, double u) {
+  if (system == 2) return u;
+  if (system == 3) {
+    const double q = 1.0 - u;
+    const double D = fma(0.25 * q, q, u * u);
+    return (0.5 * u * q) / (D * D);
+  }
+  return a;
+}
+// GLF speed of eq. (6) for a scalar flux over the data range [umin, umax]:
+// the largest |f'| there (for Buckley-Leverett f' peaks inside (0, 1) at
+// ustar, which the host supplies).
+__device__ __forceinline__ double scalar_alpha(int system, double a, double umin, double umax,
+                                               double ustar) {
+  if (system == 0) return fabs(a);
+  double s = fmax(fabs(scalar_speed(system, a, umin)), fabs(scalar_speed(system, a, umax)));
+  if (system == 3 && umin <= ustar && ustar <= umax)
+    s = fmax(s, fabs(scalar_speed(system, a, ustar)));
+  return s;
+}
+
 // Bit pattern of |x| as an ordered integer: for non-negative doubles the
 // integer order is the numeric order (NaN sorts above +inf).
 __device__ __forceinline__ unsigned long long abs_bits(double x) {

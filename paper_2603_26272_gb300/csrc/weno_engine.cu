@@ -324,7 +324,7 @@ weno_status weno_engine_admit(weno_engine *E, const weno_desc *d, const double *
   if (e == cudaSuccess) e = cudaMemsetAsync(S.steps, 0, sizeof(long long), E->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.status, 0, sizeof(DevStatus), E->s);
   if (e == cudaSuccess) {
-    weno::AlphaArgs a;
+    weno::AlphaArgs a = {};
     a.system = 1;
     a.ndim = d->ndim;
     a.nc = nc;

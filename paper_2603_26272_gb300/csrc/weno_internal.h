@@ -25,6 +25,7 @@ struct StageArgs {
   double cfl, eps, mu0, p;
   int ai, alpha_single;
   int precision;      // 0 FP64, 1 FP32 reconstruction
+  double ustar;       // Buckley-Leverett: maximiser of f' on [0, 1]
   int tile_variant;   // 2D tile shape: 0 32x16, 1 16x16, 2 16x8 (results identical)
   double adv_speed;
   // data
@@ -49,7 +50,7 @@ struct StageArgs {
 struct AlphaArgs {
   int system, ndim, nc, alpha_single;
   long long nbatch, nx, ny;
-  double dx, dy, gamma, cfl, adv_speed;
+  double dx, dy, gamma, cfl, adv_speed, ustar;
   const double *U;
   unsigned long long *alpha_out;
   DevStatus *status;
@@ -98,6 +99,9 @@ cudaError_t launch_stage(const StageArgs &a, cudaStream_t s);
 cudaError_t launch_alpha_export(const AlphaArgs &a, const unsigned long long *bits, double *alpha,
                                 double *dt, cudaStream_t s);
 cudaError_t launch_fill(double *p, long long n, double v, cudaStream_t s);
+
+// Maximiser of the Buckley-Leverett speed f' on [0, 1].
+double bl_speed_argmax();
 
 // Message returned by weno_last_error() on the calling thread.
 void set_last_error(const char *msg);

@@ -55,9 +55,18 @@ __device__ void record_status(DevStatus *st, int code, int stage, long long b, l
 // CFL step of problem b from its speed maxima (bit patterns), the rule of
 // the oracle: 1D cfl dx / max(|u|+c); 2D cfl / (max(|u|+c)/dx + max(|v|+c)/dy).
 // max(|u-c|, |u+c|) = |u| + c exactly (same rounding).
+// Scalar systems 2, 3 keep okey(max u) and okey(max -u) in slots 0 and 1.
+__device__ __forceinline__ double scalar_alpha_of(int system, double adv, double ustar,
+                                                  const unsigned long long *al) {
+  if (system == 0) return fabs(adv);
+  const double umax = okey_inv(al[0]), umin = -okey_inv(al[1]);
+  return scalar_alpha(system, adv, umin, umax, ustar);
+}
+
 __device__ double cfl_dt(int system, int ndim, int nc, double cfl, double dx, double dy,
-                         double adv, const unsigned long long *al) {
+                         double adv, const unsigned long long *al, double ustar = 0.0) {
   if (system == 0) return cfl * dx / fabs(adv);
+  if (system >= 2) return cfl * dx / scalar_alpha_of(system, adv, ustar, al);
   const unsigned long long sxb = max(al[0], al[nc == 3 ? 2 : 3]);
   const double sx = bits2d(sxb);
   if (ndim == 1) return cfl * dx / sx;
@@ -88,7 +97,7 @@ __device__ bool stage_control(const StageArgs &a, long long b, bool first_block_
         } else {
           dt = a.dt_fixed > 0.0 ? a.dt_fixed
                                 : cfl_dt(a.system, a.ndim, a.nc, a.cfl, a.dx, a.dy,
-                                         a.adv_speed, a.alpha_in + b * 8);
+                                         a.adv_speed, a.alpha_in + b * 8, a.ustar);
           const double rem = a.t_final - t;
           const bool last = !(dt < rem);
           if (last) dt = rem;
@@ -373,7 +382,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 1 : 256 / NT)) k_euler2d(cons
 // ---------------------------------------------------------------------------
 template <int NC, int T>
 constexpr size_t smem_line1d() {
-  return sizeof(double) * (((NC == 3) ? 9 : 1) * (T + 6) + (T + 1) * NC);
+  return sizeof(double) * (((NC == 3) ? 9 : 2) * (T + 6) + (T + 1) * NC);
 }
 
 // One tile of T cells (T + 1 faces, one per thread; blockDim = T + 1) of a
@@ -382,7 +391,7 @@ template <int NC, bool AI, bool P1, int PREC, int T>
 __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, long long tile,
                                             bool zeroing_block, double *sm) {
   constexpr int REG = T + 6;
-  constexpr int NP = (NC == 3) ? 9 : 1;
+  constexpr int NP = (NC == 3) ? 9 : 2;
   double(*pl)[REG] = reinterpret_cast<double(*)[REG]>(sm);
   double(*fl)[NC] = reinterpret_cast<double(*)[NC]>(sm + NP * REG);
   const long long i0 = tile * T;
@@ -396,7 +405,10 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
   for (int k = tid; k < REG; k += blockDim.x) {
     const long long gi = ghost(i0 - 3 + k, nx, a.bc_x);
     if (NC == 1) {
-      pl[0][k] = Ub[gi];
+      const double u = Ub[gi];
+      if (!(u == u) || fabs(u) > 1.7e308) record_status(a.status, 3, a.stage, b, 0, gi);
+      pl[0][k] = u;
+      pl[1][k] = scalar_flux(a.system, a.adv_speed, u);
     } else {
       const double rho = Ub[gi], m = Ub[nx + gi], E = Ub[2 * nx + gi];
       const double rs = rsqrt(rho);
@@ -422,14 +434,14 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
     const int f = tid;  // face between cells i0+f-1 and i0+f; stencil cells f..f+5
     if (f <= T && i0 + f - 1 < nx) {
       if (NC == 1) {
-        const double A = fabs(a.adv_speed), c = a.adv_speed;
+        const double A = scalar_alpha_of(a.system, a.adv_speed, a.ustar, a.alpha_in + b * 8);
         double h;
         if (PREC == 1) {
           double w[6], g[6];
 #pragma unroll
           for (int j = 0; j < 6; ++j) {
             w[j] = pl[0][f + j];
-            g[j] = c * w[j];
+            g[j] = pl[1][f + j];
           }
           h = field_flux_f32<P1>(w, g, A, make_r32(a));
         } else {
@@ -437,9 +449,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
           double pp[6], mm[6];
 #pragma unroll
           for (int j = 0; j < 6; ++j) {
-            const double v = pl[0][f + j];
-            pp[j] = fma(A, v, c * v);
-            mm[j] = fma(-A, v, c * v);
+            const double v = pl[0][f + j], fv = pl[1][f + j];
+            pp[j] = fma(A, v, fv);
+            mm[j] = fma(-A, v, fv);
           }
           h = za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp) +
               za6<AI, P1>(mm[5], mm[4], mm[3], mm[2], mm[1], mm[0], rp);
@@ -502,7 +514,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
 
   const double idx = 1.0 / a.dx;
   unsigned long long m3v[3] = {0ull, 0ull, 0ull};
-  const bool want_alpha = (NC == 3) && (a.mode == 0) && (a.alpha_out != nullptr);
+  const bool want_alpha = (NC == 3 || a.system >= 2) && (a.mode == 0) && (a.alpha_out != nullptr);
   if (tid < T && i0 + tid < nx) {
     const long long gi = i0 + tid;
     const long long o = b * NC * nx + gi;
@@ -519,7 +531,11 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
       }
       a.Uout[o + q * nx] = uo[q];
     }
-    if (want_alpha) {
+    if (want_alpha && NC == 1) {  // scalar: keys of max u and max -u
+      if (!(uo[0] == uo[0]) || fabs(uo[0]) > 1.7e308) record_status(a.status, 3, a.stage, b, 0, gi);
+      m3v[0] = okey(uo[0]);
+      m3v[1] = okey(-uo[0]);
+    } else if (want_alpha) {
       const double ir = 1.0 / uo[0];
       const double u = uo[1] * ir;
       const double p = gm1 * (uo[NC - 1] - 0.5 * (uo[1] * u));
@@ -552,6 +568,20 @@ __global__ void __launch_bounds__(256) k_alpha(const AlphaArgs a) {
   const long long b = blockIdx.y;
   const long long plane = a.nx * a.ny;
   const double *Ub = a.U + b * a.nc * plane;
+  if (a.system >= 2) {  // scalar: keys of max u and max -u
+    unsigned long long km[2] = {0ull, 0ull};
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < plane;
+         k += (long long)gridDim.x * blockDim.x) {
+      const double u = Ub[k];
+      if (!(u == u) || fabs(u) > 1.7e308) record_status(a.status, 3, 0, b, 0, k);
+      km[0] = max(km[0], okey(u));
+      km[1] = max(km[1], okey(-u));
+    }
+    const int slot[2] = {0, 1};
+    const int dup[2] = {-1, -1};
+    block_max_atomic<2>(km, a.alpha_out + b * 8, slot, dup);
+    return;
+  }
   const double gm1 = a.gamma - 1.0;
   unsigned long long vm[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < plane;
@@ -592,8 +622,8 @@ __global__ void k_alpha_export(const AlphaArgs a, const unsigned long long *bits
   const unsigned long long *al = bits + b * 8;
   if (alpha) {
     for (int k = 0; k < 8; ++k) alpha[b * 8 + k] = 0.0;
-    if (a.system == 0) {
-      alpha[b * 8] = fabs(a.adv_speed);
+    if (a.system == 0 || a.system >= 2) {
+      alpha[b * 8] = scalar_alpha_of(a.system, a.adv_speed, a.ustar, al);
     } else {
       for (int k = 0; k < 8; ++k) alpha[b * 8 + k] = bits2d(al[k]);
       if (a.alpha_single)
@@ -604,7 +634,7 @@ __global__ void k_alpha_export(const AlphaArgs a, const unsigned long long *bits
         }
     }
   }
-  if (dt) dt[b] = cfl_dt(a.system, a.ndim, a.nc, a.cfl, a.dx, a.dy, a.adv_speed, al);
+  if (dt) dt[b] = cfl_dt(a.system, a.ndim, a.nc, a.cfl, a.dx, a.dy, a.adv_speed, al, a.ustar);
 }
 
 __global__ void k_fill(double *p, long long n, double v) {
@@ -760,7 +790,7 @@ cudaError_t launch_engine_stage(const EngineArgs &e, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_alpha(const AlphaArgs &a, cudaStream_t s) {
-  if (a.system == 0) return cudaSuccess;  // advection: alpha = |a|, no reduction
+  if (a.system == 0) return cudaSuccess;  // linear advection: alpha = |a|, no reduction
   const long long plane = a.nx * a.ny;
   long long bx = (plane + 255) / 256;
   if (bx > 1024) bx = 1024;

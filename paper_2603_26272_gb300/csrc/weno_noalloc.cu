@@ -89,7 +89,7 @@ extern "C" weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, dou
   const double dx = (d->x1 - d->x0) / (double)d->nx;
   const double dy = d->ndim == 2 ? (d->y1 - d->y0) / (double)d->ny : 1.0;
 
-  weno::AlphaArgs a;
+  weno::AlphaArgs a = {};
   a.system = d->system;
   a.ndim = d->ndim;
   a.nc = nc;
@@ -102,6 +102,7 @@ extern "C" weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, dou
   a.gamma = d->gamma;
   a.cfl = d->cfl;
   a.adv_speed = d->adv_speed;
+  a.ustar = weno::bl_speed_argmax();
   a.U = U;
   a.alpha_out = slot;
   a.status = status;
@@ -127,6 +128,7 @@ extern "C" weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, dou
   r.ai = d->ai;
   r.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
   r.precision = d->precision;
+  r.ustar = weno::bl_speed_argmax();
   r.adv_speed = d->adv_speed;
   r.Uin = U;
   r.Uout = dUdt;

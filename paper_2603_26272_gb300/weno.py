@@ -19,7 +19,7 @@ WENO_ERR_NOMEM, WENO_ERR_TIMEOUT, WENO_ERR_MAXSTEPS = 4, 5, 6
 STATUS_NAMES = {0: "WENO_OK", 1: "WENO_ERR_ARG", 2: "WENO_ERR_CUDA", 3: "WENO_ERR_NONPHYSICAL",
                 4: "WENO_ERR_NOMEM", 5: "WENO_ERR_TIMEOUT", 6: "WENO_ERR_MAXSTEPS"}
 
-SYSTEMS = {"advection": 0, "euler": 1}
+SYSTEMS = {"advection": 0, "euler": 1, "burgers": 2, "buckley_leverett": 3}
 BCS = {"transmissive": 0, "periodic": 1}
 PRECISIONS = {"fp64": 0, "fp32_recon": 1}
 ALPHA_MODES = {"field": 0, "single": 1}
@@ -53,7 +53,7 @@ class Desc(ctypes.Structure):
 
     @property
     def ncomp(self):
-        return 1 if self.system == 0 else (3 if self.ndim == 1 else 4)
+        return 1 if self.system != 1 else (3 if self.ndim == 1 else 4)
 
     @property
     def shape(self):

@@ -43,6 +43,32 @@ def advection_sine(n=200, cfl=0.5, t_final=2.0):
             "exact": lambda xx, t: np.sin(np.pi * (xx - t) - np.sin(np.pi * (xx - t)) / np.pi)}
 
 
+def burgers_sine(n=80, t_final=0.2, cfl=0.5):
+    """Burgers u_t + (u^2/2)_x = 0 with u0 = 1/2 + sin(2 pi x) (Section 4.1,
+    Table 5: N = 80, T = 0.2); reading: periodic [0, 1], one period of u0."""
+    x, dx = cell_centres(0.0, 1.0, n)
+    return {"system": "burgers", "ndim": 1, "U": (0.5 + np.sin(2 * np.pi * x)).reshape(1, 1, 1, n),
+            "x": x, "dx": dx, "domain": (0.0, 1.0), "n": n, "bc": "periodic", "cfl": cfl,
+            "t_final": t_final}
+
+
+def buckley_leverett(n=200, t_final=0.3, cfl=0.5, a=-1.0, b=1.0):
+    """Buckley-Leverett with u0 = 1 on [-0.5, 0], 0 elsewhere (Section 4.1,
+    Table 5: N = 200, T = 0.3); reading: transmissive [-1, 1]."""
+    x, dx = cell_centres(a, b, n)
+    u0 = np.where((x >= -0.5) & (x <= 0.0), 1.0, 0.0)
+    return {"system": "buckley_leverett", "ndim": 1, "U": u0.reshape(1, 1, 1, n), "x": x, "dx": dx,
+            "domain": (a, b), "n": n, "bc": "transmissive", "cfl": cfl, "t_final": t_final}
+
+
+def buckley_riemann(n=400, t_final=0.3, cfl=0.5, a=-1.0, b=1.0):
+    """Buckley-Leverett Riemann problem u = 1 for x < 0, u = 0 for x > 0."""
+    x, dx = cell_centres(a, b, n)
+    return {"system": "buckley_leverett", "ndim": 1, "U": np.where(x < 0, 1.0, 0.0).reshape(1, 1, 1, n),
+            "x": x, "dx": dx, "domain": (a, b), "n": n, "bc": "transmissive", "cfl": cfl,
+            "t_final": t_final}
+
+
 def shock_density(n=1600, a=-5.0, b=5.0, t_final=1.8, cfl=0.5, gamma=GAMMA):
     """Mach-3 shock meeting a density wave (Section 4.2, shock-density example):
     (3.857143, 2.629369, 10.33333) for x < -4, (1 + 0.2 sin 5x, 0, 1) beyond."""
