@@ -34,6 +34,8 @@ class OraGrid(ctypes.Structure):
         ("ai", ctypes.c_int32),
         ("alpha_mode", ctypes.c_int32),
         ("adv_speed", ctypes.c_double),
+        ("order", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -55,6 +57,10 @@ def lib():
                                         ctypes.c_int]
         L.ora_coefficients.restype = None
         L.ora_coefficients.argtypes = [_D]
+        L.ora_za_flux.restype = ctypes.c_double
+        L.ora_za_flux.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int]
+        L.ora_coefficients_r.argtypes = [ctypes.c_int, _D]
         L.ora_operator_error.restype = ctypes.c_double
         L.ora_operator_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int]
@@ -89,7 +95,7 @@ def _check(code, what):
 
 def make_grid(system="euler", ndim=1, nbatch=1, nx=1, ny=1, dx=1.0, dy=1.0, bc_x="transmissive",
               bc_y="transmissive", gamma=1.4, eps=1e-40, mu0=1e-40, p=1.0, ai=1,
-              alpha_mode="field", adv_speed=1.0):
+              alpha_mode="field", adv_speed=1.0, order=6):
     bcs = {"transmissive": 0, "periodic": 1}
     g = OraGrid()
     g.system = {"advection": 0, "euler": 1, "burgers": 2, "buckley_leverett": 3}[system]
@@ -108,6 +114,7 @@ def make_grid(system="euler", ndim=1, nbatch=1, nx=1, ny=1, dx=1.0, dy=1.0, bc_x
     g.ai = int(ai)
     g.alpha_mode = {"field": 0, "single": 1}[alpha_mode]
     g.adv_speed = adv_speed
+    g.order = order
     return g
 
 
@@ -145,6 +152,27 @@ def coefficients():
     return {"c6": out[0:6], "ck": out[6:18].reshape(4, 3), "d": out[18:22],
             "B0": out[22:31].reshape(3, 3), "B1": out[31:40].reshape(3, 3),
             "B2": out[40:49].reshape(3, 3), "Bd": out[49:58].reshape(3, 3), "ctau": out[58:64]}
+
+
+def za_flux(order, f, eps=1e-40, mu0=1e-40, p=1.0, ai=1):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    assert f.shape == (order,)
+    return lib().ora_za_flux(int(order), _p(f), eps, mu0, p, int(ai))
+
+
+def coefficients_r(order):
+    r = order // 2
+    n = 2 * r + (r + 1) * r + (r + 1) + (r + 1) * r * r + 2 * r
+    out = np.zeros(n)
+    _check(lib().ora_coefficients_r(int(order), _p(out)), "ora_coefficients_r")
+    o = 0
+    res = {}
+    for name, size, shape in (("c2r", 2 * r, (2 * r,)), ("ck", (r + 1) * r, (r + 1, r)),
+                              ("d", r + 1, (r + 1,)), ("B", (r + 1) * r * r, (r + 1, r, r)),
+                              ("ctau", 2 * r, (2 * r,))):
+        res[name] = out[o:o + size].reshape(shape)
+        o += size
+    return res
 
 
 def operator_error(ncp, inv_dx, p=1.0, eps_variable=False, quad=False):

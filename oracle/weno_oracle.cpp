@@ -201,6 +201,169 @@ double za6(const double f[6], double eps, double mu0, double p, int ai) {
 }
 
 // ---------------------------------------------------------------------------
+// Appendix: the fourth-, eighth- and tenth-order schemes (r = 2, 4, 5), with
+// the coefficient tables as printed there; the sixth-order tables of
+// Section 3 give r = 3.  Rows written "rev(.)" in the paper are reversed here.
+// ---------------------------------------------------------------------------
+struct OrderTable {
+  int r;
+  std::vector<int> c2r;                         // eq. (10) analogue, / c2r_den
+  int c2r_den;
+  std::vector<std::vector<int>> ck;             // r + 1 rows of r, / ck_den
+  int ck_den;
+  std::vector<int> d;                           // r + 1, / d_den
+  int d_den;
+  std::vector<std::vector<std::vector<int>>> B;  // B_0 .. B_{r-1}, B_d (r x r), / b_den
+  int b_den;
+  std::vector<int> ctau;                        // 2r
+};
+
+std::vector<int> rev1(const std::vector<int> &v) { return std::vector<int>(v.rbegin(), v.rend()); }
+std::vector<std::vector<int>> rev2(const std::vector<std::vector<int>> &M) {
+  const int n = (int)M.size();
+  std::vector<std::vector<int>> R(n, std::vector<int>(n));
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) R[a][b] = M[n - 1 - a][n - 1 - b];
+  return R;
+}
+
+OrderTable make_table(int r) {
+  OrderTable t;
+  t.r = r;
+  if (r == 2) {  // Appendix A.1
+    t.c2r = {-1, 7, 7, -1};
+    t.c2r_den = 12;
+    std::vector<int> c0 = {-1, 3}, c1 = {1, 1};
+    t.ck = {c0, c1, rev1(c0)};
+    t.ck_den = 2;
+    t.d = {1, 4, 1};
+    t.d_den = 6;
+    std::vector<std::vector<int>> B0 = {{1, -1}, {-1, 1}}, Bd = {{1, -1}, {-1, 1}};
+    t.B = {B0, rev2(B0), Bd};
+    t.b_den = 1;
+    t.ctau = {-1, 3, -3, 1};
+  } else if (r == 3) {  // Section 3
+    t.c2r = {1, -8, 37, 37, -8, 1};
+    t.c2r_den = 60;
+    t.ck = {{2, -7, 11}, {-1, 5, 2}, {2, 5, -1}, {11, -7, 2}};
+    t.ck_den = 6;
+    t.d = {1, 9, 9, 1};
+    t.d_den = 20;
+    std::vector<std::vector<int>> B0 = {{8, -19, 11}, {-19, 50, -31}, {11, -31, 20}};
+    std::vector<std::vector<int>> B1 = {{8, -13, 5}, {-13, 26, -13}, {5, -13, 8}};
+    std::vector<std::vector<int>> Bd = {{44, -73, 29}, {-73, 122, -49}, {29, -49, 20}};
+    t.B = {B0, B1, rev2(B0), Bd};
+    t.b_den = 6;
+    t.ctau = {-1, 5, -10, 10, -5, 1};
+  } else if (r == 4) {  // Appendix A.2
+    t.c2r = {-3, 29, -139, 533, 533, -139, 29, -3};
+    t.c2r_den = 840;
+    std::vector<int> c0 = {-3, 13, -23, 25}, c1 = {1, -5, 13, 3}, c2 = {-1, 7, 7, -1};
+    t.ck = {c0, c1, c2, rev1(c1), rev1(c0)};
+    t.ck_den = 12;
+    t.d = {1, 16, 36, 16, 1};
+    t.d_den = 70;
+    std::vector<std::vector<int>> B0 = {{547, -1941, 2321, -927}, {-1941, 7043, -8623, 3521},
+                                        {2321, -8623, 11003, -4701}, {-927, 3521, -4701, 2107}};
+    std::vector<std::vector<int>> B1 = {{267, -821, 801, -247}, {-821, 2843, -2983, 961},
+                                        {801, -2983, 3443, -1261}, {-247, 961, -1261, 547}};
+    std::vector<std::vector<int>> Bd = {{7107, -16901, 13521, -3727}, {-16901, 40643, -32863, 9121},
+                                        {13521, -32863, 26843, -7501}, {-3727, 9121, -7501, 2107}};
+    t.B = {B0, B1, rev2(B1), rev2(B0), Bd};
+    t.b_den = 240;
+    t.ctau = {-1, 7, -21, 35, -35, 21, -7, 1};
+  } else {  // r == 5, Appendix A.3
+    t.c2r = {2, -23, 127, -473, 1627, 1627, -473, 127, -23, 2};
+    t.c2r_den = 2520;
+    std::vector<int> c0 = {12, -63, 137, -163, 137}, c1 = {-3, 17, -43, 77, 12},
+                     c2 = {2, -13, 47, 27, -3};
+    t.ck = {c0, c1, c2, rev1(c2), rev1(c1), rev1(c0)};
+    t.ck_den = 60;
+    t.d = {1, 25, 100, 100, 25, 1};
+    t.d_den = 252;
+    std::vector<std::vector<int>> B0 = {{45316, -208501, 364863, -288007, 86329},
+                                        {-208501, 965926, -1704396, 1358458, -411487},
+                                        {364863, -1704396, 3042786, -2462076, 758823},
+                                        {-288007, 1358458, -2462076, 2041126, -649501},
+                                        {86329, -411487, 758823, -649501, 215836}};
+    std::vector<std::vector<int>> B1 = {{13816, -60871, 99213, -70237, 18079},
+                                        {-60871, 277126, -464976, 337018, -88297},
+                                        {99213, -464976, 812586, -611976, 165153},
+                                        {-70237, 337018, -611976, 485446, -140251},
+                                        {18079, -88297, 165153, -140251, 45316}};
+    std::vector<std::vector<int>> B2 = {{13816, -51001, 67923, -38947, 8209},
+                                        {-51001, 209926, -299076, 179098, -38947},
+                                        {67923, -299076, 462306, -299076, 67923},
+                                        {-38947, 179098, -299076, 209926, -51001},
+                                        {8209, -38947, 67923, -51001, 13816}};
+    std::vector<std::vector<int>> Bd = {{942016, -2964751, 3597813, -2004757, 429679},
+                                        {-2964751, 9449926, -11584896, 6499258, -1399537},
+                                        {3597813, -11584896, 14319786, -8079576, 1746873},
+                                        {-2004757, 6499258, -8079576, 4577926, -992851},
+                                        {429679, -1399537, 1746873, -992851, 215836}};
+    t.B = {B0, B1, B2, rev2(B1), rev2(B0), Bd};
+    t.b_den = 10080;
+    t.ctau = {-1, 9, -36, 84, -126, 126, -84, 36, -9, 1};
+  }
+  return t;
+}
+
+const OrderTable &table_of(int r) {
+  static const OrderTable t2 = make_table(2), t3 = make_table(3), t4 = make_table(4),
+                          t5 = make_table(5);
+  return r == 2 ? t2 : (r == 3 ? t3 : (r == 4 ? t4 : t5));
+}
+
+// Central-upwind WENO flux of order 2r at x_{i+1/2} from f[0 .. 2r-1] =
+// f_{i-r+1} .. f_{i+r} (Section 2: eqs. (9)-(22) with the tables above; the
+// downwind indicator is the mean of all r + 1 local ones, eq. (16)).  The
+// indicators are evaluated on shifted data as in za6_flux.
+double zar_flux(int r, const double *f, double eps, double mu0, double p, int ai) {
+  const OrderTable &t = table_of(r);
+  const int n = 2 * r;
+  std::vector<double> fk(r + 1), beta(r + 1);
+  for (int k = 0; k <= r; ++k) {  // candidate fluxes on S_k
+    double s = 0;
+    for (int m = 0; m < r; ++m) s += (double)t.ck[k][m] * f[k + m];
+    fk[k] = s / t.ck_den;
+  }
+  double bsum = 0;
+  for (int k = 0; k <= r; ++k) {  // beta_0 .. beta_{r-1} and beta_d (k = r)
+    std::vector<double> g(r);
+    for (int m = 0; m < r; ++m) g[m] = f[k + m] - f[k];
+    double s = 0;
+    for (int a = 0; a < r; ++a)
+      for (int b = 0; b < r; ++b) s += g[a] * (double)t.B[k][a][b] * g[b];
+    s /= t.b_den;
+    if (k < r) beta[k] = s;
+    bsum += s;
+  }
+  beta[r] = bsum / (r + 1);  // eq. (16)
+  double mean = 0;
+  for (int j = 0; j < n; ++j) mean += f[j];
+  mean /= n;
+  double tr = 0;
+  for (int j = 0; j < n; ++j) tr += (double)t.ctau[j] * (f[j] - mean);
+  const double tau = tr * tr;  // eq. (17)
+  double mu = 1;
+  if (ai) {  // eq. (22)
+    double dev = 0;
+    for (int j = 0; j < n; ++j) dev += std::fabs(f[j] - mean);
+    mu = dev / n + mu0;
+  }
+  double asum = 0;
+  std::vector<double> al(r + 1);
+  for (int k = 0; k <= r; ++k) {  // eqs. (19)-(21), L = q = 1
+    const double G = r_pow<double>(tau / (beta[k] + eps * mu * mu), p);
+    al[k] = ((double)t.d[k] / t.d_den) * (1.0 + G);
+    asum += al[k];
+  }
+  double fh = 0;
+  for (int k = 0; k <= r; ++k) fh += (al[k] / asum) * fk[k];  // eq. (14)
+  return fh;
+}
+
+// ---------------------------------------------------------------------------
 // Euler equations (Section 4.2, eq. (25); its 2D form for Section 4.3).
 // State order: (rho, rho u, E) in 1D, (rho, rho u, rho v, E) in 2D.
 // ---------------------------------------------------------------------------
@@ -384,30 +547,44 @@ int64_t ghost(int64_t k, int64_t n, int bc) {
 // flux are projected on the left eigenvectors, split by eq. (6) field by
 // field, reconstructed by WENO-ZA6 (positive flux on the stencil, negative
 // flux on its mirror image) and projected back with the right eigenvectors.
-int face_flux(const ora_grid *g, int dir, const double st[6][4], const double *alpha,
+int order_r(const ora_grid *g) {
+  const int o = g->order == 0 ? 6 : g->order;
+  return o / 2;
+}
+
+// One WENO flux of the grid's order from n = 2r values.
+double weno_flux(const ora_grid *g, const double *f) {
+  const int r = order_r(g);
+  if (r == 3) return za6(f, g->eps, g->mu0, g->p, g->ai);
+  return zar_flux(r, f, g->eps, g->mu0, g->p, g->ai);
+}
+
+int face_flux(const ora_grid *g, int dir, const double st[10][4], const double *alpha,
               double *Fhat) {
   const int nc = ncomp_of(g);
+  const int r = order_r(g), n = 2 * r;
   if (g->system != 1) {
-    double fp[6], fm[6];
-    for (int j = 0; j < 6; ++j) {
+    double fp[10], fm[10];
+    for (int j = 0; j < n; ++j) {
       double f = scalar_flux(g, st[j][0]);
       fp[j] = 0.5 * (f + alpha[0] * st[j][0]);
-      fm[5 - j] = 0.5 * (f - alpha[0] * st[j][0]);
+      fm[n - 1 - j] = 0.5 * (f - alpha[0] * st[j][0]);
     }
-    Fhat[0] = za6(fp, g->eps, g->mu0, g->p, g->ai) + za6(fm, g->eps, g->mu0, g->p, g->ai);
+    Fhat[0] = weno_flux(g, fp) + weno_flux(g, fm);
     return 0;
   }
-  Prim w[6];
-  double F[6][4];
-  for (int j = 0; j < 6; ++j) {
+  Prim w[10];
+  double F[10][4];
+  for (int j = 0; j < n; ++j) {
     if (!to_prim(nc, st[j], g->gamma, &w[j])) return 2;
     euler_flux(nc, dir, st[j], w[j], F[j]);
   }
-  // Roe average of cells i (stencil index 2) and i+1 (index 3).
-  double sl = std::sqrt(w[2].rho), sr = std::sqrt(w[3].rho);
-  double u = (sl * w[2].u + sr * w[3].u) / (sl + sr);
-  double v = (sl * w[2].v + sr * w[3].v) / (sl + sr);
-  double H = (sl * w[2].H + sr * w[3].H) / (sl + sr);
+  // Roe average of cells i (stencil index r-1) and i+1 (index r).
+  const Prim &wl = w[r - 1], &wr = w[r];
+  double sl = std::sqrt(wl.rho), sr = std::sqrt(wr.rho);
+  double u = (sl * wl.u + sr * wr.u) / (sl + sr);
+  double v = (sl * wl.v + sr * wr.v) / (sl + sr);
+  double H = (sl * wl.H + sr * wr.H) / (sl + sr);
   double c2 = (g->gamma - 1.0) * (H - 0.5 * (u * u + v * v));
   if (!(c2 > 0) || !finite(c2)) return 2;
   double c = std::sqrt(c2);
@@ -416,39 +593,40 @@ int face_flux(const ora_grid *g, int dir, const double st[6][4], const double *a
   if (!invert(nc, R, L)) return 2;
   double h[4];
   for (int m = 0; m < nc; ++m) {
-    double fp[6], fm[6];
-    for (int j = 0; j < 6; ++j) {
+    double fp[10], fm[10];
+    for (int j = 0; j < n; ++j) {
       double wc = 0, gc = 0;
       for (int k = 0; k < nc; ++k) {
         wc += L[m][k] * st[j][k];
         gc += L[m][k] * F[j][k];
       }
-      fp[j] = 0.5 * (gc + alpha[m] * wc);      // f^+ of eq. (6)
-      fm[5 - j] = 0.5 * (gc - alpha[m] * wc);  // f^- of eq. (6), mirrored
+      fp[j] = 0.5 * (gc + alpha[m] * wc);          // f^+ of eq. (6)
+      fm[n - 1 - j] = 0.5 * (gc - alpha[m] * wc);  // f^- of eq. (6), mirrored
     }
-    h[m] = za6(fp, g->eps, g->mu0, g->p, g->ai) + za6(fm, g->eps, g->mu0, g->p, g->ai);
+    h[m] = weno_flux(g, fp) + weno_flux(g, fm);
   }
-  for (int r = 0; r < nc; ++r) {
-    double s = 0;
-    for (int m = 0; m < nc; ++m) s += R[r][m] * h[m];
-    Fhat[r] = s;
+  for (int rr = 0; rr < nc; ++rr) {
+    double sum = 0;
+    for (int m = 0; m < nc; ++m) sum += R[rr][m] * h[m];
+    Fhat[rr] = sum;
   }
   return 0;
 }
 
-// Load the 6-cell stencil of face (i+1/2) along x in row j, or of face
-// (j+1/2) along y in column i, of problem b.
+// Load the 2r-cell stencil of face (i+1/2) along x in row j (cells i-r+1 ..
+// i+r), or of face (j+1/2) along y in column i, of problem b.
 void load_stencil(const ora_grid *g, const double *U, int64_t b, int dir, int64_t j, int64_t i,
-                  double st[6][4]) {
+                  double st[10][4]) {
   const int nc = ncomp_of(g);
+  const int r = order_r(g);
   const int64_t nx = g->nx, ny = g->ny;
   const double *Ub = U + b * nc * nx * ny;
-  for (int s = 0; s < 6; ++s) {
+  for (int s = 0; s < 2 * r; ++s) {
     int64_t ii = i, jj = j;
     if (dir == 0)
-      ii = ghost(i - 2 + s, nx, g->bc_x);
+      ii = ghost(i - r + 1 + s, nx, g->bc_x);
     else
-      jj = ghost(j - 2 + s, ny, g->bc_y);
+      jj = ghost(j - r + 1 + s, ny, g->bc_y);
     for (int k = 0; k < nc; ++k) st[s][k] = Ub[(k * ny + jj) * nx + ii];
   }
 }
@@ -458,6 +636,7 @@ int check_grid(const ora_grid *g) {
   if (g->ndim != 1 && g->ndim != 2) return 1;
   if (g->ndim == 1 && g->ny != 1) return 1;
   if (g->system < 0 || g->system > 3) return 1;
+  if (g->order != 0 && g->order != 4 && g->order != 6 && g->order != 8 && g->order != 10) return 1;
   if (g->system != 1 && g->ndim != 1) return 1;
   return 0;
 }
@@ -466,7 +645,7 @@ int check_grid(const ora_grid *g) {
 int rhs_cell(const ora_grid *g, const double *U, const double *alpha, int64_t b, int64_t j,
              int64_t i, double *out) {
   const int nc = ncomp_of(g);
-  double st[6][4], Fl[4], Fr[4];
+  double st[10][4], Fl[4], Fr[4];
   const double *al = alpha + b * 8;
   load_stencil(g, U, b, 0, j, i - 1, st);
   int e = face_flux(g, 0, st, al, Fl);
@@ -556,6 +735,28 @@ double ora_za6_flux_quad(const double f[6], double eps, double mu0, double p, in
   return (double)o.fhat;
 }
 
+double ora_za_flux(int order, const double *f, double eps, double mu0, double p, int ai) {
+  const int r = order / 2;
+  if (r < 2 || r > 5 || 2 * r != order) return NAN;
+  return zar_flux(r, f, eps, mu0, p, ai);
+}
+
+int ora_coefficients_r(int order, double *out) {
+  const int r = order / 2;
+  if (r < 2 || r > 5 || 2 * r != order) return 1;
+  const OrderTable &t = table_of(r);
+  int n = 0;
+  for (int j = 0; j < 2 * r; ++j) out[n++] = (double)t.c2r[j] / t.c2r_den;
+  for (int k = 0; k <= r; ++k)
+    for (int m = 0; m < r; ++m) out[n++] = (double)t.ck[k][m] / t.ck_den;
+  for (int k = 0; k <= r; ++k) out[n++] = (double)t.d[k] / t.d_den;
+  for (int k = 0; k <= r; ++k)
+    for (int a = 0; a < r; ++a)
+      for (int b = 0; b < r; ++b) out[n++] = (double)t.B[k][a][b] / t.b_den;
+  for (int j = 0; j < 2 * r; ++j) out[n++] = (double)t.ctau[j];
+  return 0;
+}
+
 void ora_coefficients(double *out) {
   int n = 0;
   for (int j = 0; j < 6; ++j) out[n++] = (double)C6_NUM[j] / C6_DEN;
@@ -638,7 +839,7 @@ int ora_rhs(const ora_grid *g, const double *U, const double *alpha, double *L) 
     // x sweep: faces i+1/2 for i = -1 .. nx-1 of every row.
     for (int64_t j = 0; j < ny; ++j) {
       for (int64_t i = -1; i < nx; ++i) {
-        double st[6][4];
+        double st[10][4];
         load_stencil(g, U, b, 0, j, i, st);
         int e = face_flux(g, 0, st, al, &Fx[(size_t)(i + 1) * 4]);
         if (e) return e;
@@ -651,7 +852,7 @@ int ora_rhs(const ora_grid *g, const double *U, const double *alpha, double *L) 
     // y sweep: faces j+1/2 for j = -1 .. ny-1 of every column.
     for (int64_t i = 0; i < nx; ++i) {
       for (int64_t j = -1; j < ny; ++j) {
-        double st[6][4];
+        double st[10][4];
         load_stencil(g, U, b, 1, j, i, st);
         int e = face_flux(g, 1, st, al + 4, &Gy[(size_t)(j + 1) * 4]);
         if (e) return e;

@@ -43,6 +43,8 @@ typedef struct {
   int32_t ai;       /* 1: affine-invariant descaler mu[f] of eq. (22); 0: mu=1  */
   int32_t alpha_mode; /* 0: GLF alpha per characteristic field, 1: one alpha   */
   double adv_speed; /* a of the scalar advection equation                       */
+  int32_t order;    /* 2r: 4, 6 (also 0), 8 or 10 -- the Appendix schemes        */
+  int32_t pad;
 } ora_grid;
 
 /* WENO-ZA6 positive numerical flux at x_{i+1/2} from f = (f_{i-2}, ..., f_{i+3})
@@ -54,6 +56,14 @@ double ora_za6_flux(const double f[6], double eps, double mu0, double p, int ai,
 
 /* The same flux in quadruple precision (f given as doubles; p in {1, 1.5, 2}). */
 double ora_za6_flux_quad(const double f[6], double eps, double mu0, double p, int ai);
+
+/* Central-upwind WENO flux of order 2r (r = 2..5; Section 2 with the tables of
+ * Section 3 and the Appendix) from f_{i-r+1} .. f_{i+r}; NaN for a bad order. */
+double ora_za_flux(int order, const double *f, double eps, double mu0, double p, int ai);
+
+/* Tables of order 2r: c_2r[2r], c_k[(r+1) r], d[r+1], B_0..B_{r-1}, B_d
+ * [(r+1) r r], c_tau[2r].  Returns 1 for a bad order. */
+int ora_coefficients_r(int order, double *out);
 
 /* Coefficient tables used by the oracle, for the pins: c6[6] (eq. (10)),
  * ck[4][3] (eq. (11)), d[4] (eq. (12)), B0, B1, B2, Bd [3][3] (eq. (15)),
