@@ -49,7 +49,8 @@ FLOPS_PER_CELL_STAGE = 2 * FLOPS_PER_FACE + FLOPS_PER_CELL
 # FP64 peak: the nominal GB300 figure, 1.25 TFLOP/s (152 SMs x 2 FP64 FMA
 # lanes x 2 flop x ~2.06 GHz).
 FP64_PEAK_TFLOPS = 1.25
-KERNEL_SOURCES = ["paper_2603_26272_gb300/csrc/weno_kernels.cu",
+KERNEL_SOURCES = ["paper_2603_26272_gb300/csrc/weno_tiles.cuh",
+                  "paper_2603_26272_gb300/csrc/weno_kernels.cu",
                   "paper_2603_26272_gb300/csrc/weno_device.cuh"]
 
 
@@ -159,6 +160,37 @@ def precision_modes(weno, wl, torch, n=4096, steps=4, warmup=3):
         torch.cuda.empty_cache()
     out["fp32_recon_speedup"] = out["fp32_recon"]["value"] / out["fp64"]["value"]
     out["error_vs_fp64_oracle"] = "profiles/fp32_recon_error_512.md"
+    return out
+
+
+def scheme_orders(weno, wl, torch, n=N_GRID, steps=4, warmup=3):
+    """The central-upwind family at orders 4, 6, 8 and 10 (the Appendix
+    schemes beside WENO-ZA6) on the same 2D workload, FP64, device-timed
+    SSP-RK3 steps."""
+    w = wl.quadrant_2d(n=n, seed=SEED)
+    out = {"workload": "2D Euler %dx%d four-quadrant Riemann data (seed %d), SSP-RK3 CFL 0.5, "
+                       "FP64" % (n, n, SEED)}
+    U0 = torch.from_numpy(w["U"])
+    stream = torch.cuda.current_stream()
+    for order in (4, 6, 8, 10):
+        d = weno.desc_for(w, order=order)
+        U = U0.cuda()
+        ws = weno.workspace(d)
+        for _ in range(warmup):
+            weno.step(d, U, ws=ws, sync=False)
+        weno.sync_status(d, ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            weno.step(d, U, ws=ws, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        weno.sync_status(d, ws)
+        ms = a.elapsed_time(b) / steps
+        out["order%d" % order] = {"value": n * n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                                  "steps": steps, "warmup": warmup}
+        del U, ws
+        torch.cuda.empty_cache()
     return out
 
 
@@ -286,6 +318,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-modes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-orders", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=100)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -405,6 +438,9 @@ def main():
         torch.cuda.empty_cache()
         result["precision_modes"] = precision_modes(weno, wl, torch)
         result["gpu_launches_precision_modes"] = 4 * 2 * (4 + 3)
+    if not args.no_orders:
+        result["scheme_orders"] = scheme_orders(weno, wl, torch)
+        result["gpu_launches_scheme_orders"] = 4 * 4 * (4 + 3)
     if not args.no_serving and rank == 0:
         log("serving stream ...")
         result["serving"] = serving(args.serving_requests)

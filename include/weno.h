@@ -70,7 +70,7 @@ typedef struct weno_desc {
   int64_t nx, ny;     /* cells per axis, nx >= 1, ny >= 1 (ny = 1 when ndim = 1)  */
   double x0, x1;      /* domain [x0, x1]                                          */
   double y0, y1;      /* domain [y0, y1] (ignored in 1D)                          */
-  int32_t bc_x, bc_y; /* WENO_BC_*: 3 ghost cells per side, zero-gradient or wrap */
+  int32_t bc_x, bc_y; /* WENO_BC_*: r ghost cells per side, zero-gradient or wrap */
   double gamma;       /* ratio of specific heats (Euler)                          */
   double cfl;         /* CFL number of the time step rule                         */
   double eps;         /* sensitivity epsilon of eq. (21)                          */
@@ -80,7 +80,11 @@ typedef struct weno_desc {
   int32_t precision;  /* WENO_PREC_FP64 (FP32_RECON is reserved)                  */
   int32_t alpha_mode; /* WENO_ALPHA_FIELD: GLF speed per characteristic field;    */
                       /* WENO_ALPHA_SINGLE: one speed max|u|+c for all fields     */
-  int32_t reserved;   /* must be 0                                                */
+  int32_t order;      /* 2r, the order of the central-upwind scheme: 0 or 6 =      */
+                      /* WENO-ZA6 (Section 3); 4, 8, 10 = the schemes of the      */
+                      /* Appendix (tables of c_k, d_k, B_k, c_tau for r = 2, 4, 5) */
+                      /* with the same weights, eqs. (16)-(22).  WENO_PREC_FP32_  */
+                      /* RECON and the serving engine take order 6 only.          */
   double adv_speed;   /* a of the advection equation                              */
 } weno_desc;
 

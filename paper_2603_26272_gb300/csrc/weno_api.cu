@@ -115,7 +115,10 @@ weno_status check_desc(const weno_desc *d) {
                               "the affine-invariant weights)");
   if (d->alpha_mode != WENO_ALPHA_FIELD && d->alpha_mode != WENO_ALPHA_SINGLE)
     return fail(WENO_ERR_ARG, "alpha_mode must be WENO_ALPHA_FIELD or WENO_ALPHA_SINGLE");
-  if (d->reserved != 0) return fail(WENO_ERR_ARG, "reserved must be 0");
+  if (d->order != 0 && d->order != 4 && d->order != 6 && d->order != 8 && d->order != 10)
+    return fail(WENO_ERR_ARG, "order must be 0 (= 6), 4, 6, 8 or 10");
+  if (d->precision == WENO_PREC_FP32_RECON && d->order != 0 && d->order != 6)
+    return fail(WENO_ERR_ARG, "WENO_PREC_FP32_RECON is implemented for order 6 only");
   if (d->system == WENO_SYS_ADVECTION && !(std::fabs(d->adv_speed) > 0.0 && std::isfinite(d->adv_speed)))
     return fail(WENO_ERR_ARG, "adv_speed must be finite and non-zero");
   return WENO_OK;
@@ -192,6 +195,7 @@ StageArgs stage_args(const Ctx &c) {
   a.ai = d->ai;
   a.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
   a.precision = d->precision;
+  a.order_r = d->order == 0 ? 3 : d->order / 2;
   a.ustar = weno::bl_speed_argmax();
   a.adv_speed = d->adv_speed;
   a.t_final = INFINITY;
@@ -285,7 +289,7 @@ int tile_override() {
 weno_status choose_tile(const Ctx &c, const double *U, const unsigned long long *alpha, int *out) {
   *out = 0;
   const weno_desc *d = c.d;
-  if (d->ndim != 2) return WENO_OK;
+  if (d->ndim != 2 || (d->order != 0 && d->order != 6)) return WENO_OK;  // one tile shape
   const int forced = tile_override();
   if (forced >= 0) {
     *out = forced;

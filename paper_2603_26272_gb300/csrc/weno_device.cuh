@@ -178,6 +178,172 @@ __device__ __forceinline__ double za6(double v0, double v1, double v2, double v3
 }
 
 // ---------------------------------------------------------------------------
+// Central-upwind WENO of order 2R for R = 2, 4, 5 (the Appendix schemes; R = 3
+// uses za6 above).  Tables as printed in the Appendix, divided out; rows the
+// paper writes as rev(.) are spelled out reversed.  The candidate fluxes are
+// formed as v_{R-1} plus a correction (every c_k sums to 1); each indicator
+// beta_k = <f_k, B_k f_k> is evaluated on f_k minus its first entry (B_k
+// annihilates constants, so this is the same number with rounding relative to
+// the substencil's variation) and clamped at 0 against rounding; the weights
+// follow eqs. (16)-(21) with one division per candidate.
+// ---------------------------------------------------------------------------
+template <int R> struct OrderTab;
+
+template <> struct OrderTab<2> {
+  __device__ static double ck(int k, int m) {
+    const double c[3][2] = {{-1, 3}, {1, 1}, {3, -1}};
+    return c[k][m] / 2.0;
+  }
+  __device__ static double d(int k) {
+    const double v[3] = {1, 4, 1};
+    return v[k] / 6.0;
+  }
+  __device__ static double B(int k, int a, int b) {  // B_0 = B_1 = B_d
+    return (a == b) ? 1.0 : -1.0;
+  }
+  __device__ static double ctau(int j) {
+    const double v[4] = {-1, 3, -3, 1};
+    return v[j];
+  }
+};
+
+template <> struct OrderTab<4> {
+  __device__ static double ck(int k, int m) {
+    const double c[5][4] = {{-3, 13, -23, 25}, {1, -5, 13, 3}, {-1, 7, 7, -1}, {3, 13, -5, 1},
+                            {25, -23, 13, -3}};
+    return c[k][m] / 12.0;
+  }
+  __device__ static double d(int k) {
+    const double v[5] = {1, 16, 36, 16, 1};
+    return v[k] / 70.0;
+  }
+  __device__ static double B(int k, int a, int b) {
+    const double B0[4][4] = {{547, -1941, 2321, -927}, {-1941, 7043, -8623, 3521},
+                             {2321, -8623, 11003, -4701}, {-927, 3521, -4701, 2107}};
+    const double B1[4][4] = {{267, -821, 801, -247}, {-821, 2843, -2983, 961},
+                             {801, -2983, 3443, -1261}, {-247, 961, -1261, 547}};
+    const double Bd[4][4] = {{7107, -16901, 13521, -3727}, {-16901, 40643, -32863, 9121},
+                             {13521, -32863, 26843, -7501}, {-3727, 9121, -7501, 2107}};
+    double v;
+    if (k == 0) v = B0[a][b];
+    else if (k == 1) v = B1[a][b];
+    else if (k == 2) v = B1[3 - a][3 - b];
+    else if (k == 3) v = B0[3 - a][3 - b];
+    else v = Bd[a][b];
+    return v / 240.0;
+  }
+  __device__ static double ctau(int j) {
+    const double v[8] = {-1, 7, -21, 35, -35, 21, -7, 1};
+    return v[j];
+  }
+};
+
+template <> struct OrderTab<5> {
+  __device__ static double ck(int k, int m) {
+    const double c[6][5] = {{12, -63, 137, -163, 137}, {-3, 17, -43, 77, 12},
+                            {2, -13, 47, 27, -3},      {-3, 27, 47, -13, 2},
+                            {12, 77, -43, 17, -3},     {137, -163, 137, -63, 12}};
+    return c[k][m] / 60.0;
+  }
+  __device__ static double d(int k) {
+    const double v[6] = {1, 25, 100, 100, 25, 1};
+    return v[k] / 252.0;
+  }
+  __device__ static double B(int k, int a, int b) {
+    const double B0[5][5] = {{45316, -208501, 364863, -288007, 86329},
+                             {-208501, 965926, -1704396, 1358458, -411487},
+                             {364863, -1704396, 3042786, -2462076, 758823},
+                             {-288007, 1358458, -2462076, 2041126, -649501},
+                             {86329, -411487, 758823, -649501, 215836}};
+    const double B1[5][5] = {{13816, -60871, 99213, -70237, 18079},
+                             {-60871, 277126, -464976, 337018, -88297},
+                             {99213, -464976, 812586, -611976, 165153},
+                             {-70237, 337018, -611976, 485446, -140251},
+                             {18079, -88297, 165153, -140251, 45316}};
+    const double B2[5][5] = {{13816, -51001, 67923, -38947, 8209},
+                             {-51001, 209926, -299076, 179098, -38947},
+                             {67923, -299076, 462306, -299076, 67923},
+                             {-38947, 179098, -299076, 209926, -51001},
+                             {8209, -38947, 67923, -51001, 13816}};
+    const double Bd[5][5] = {{942016, -2964751, 3597813, -2004757, 429679},
+                             {-2964751, 9449926, -11584896, 6499258, -1399537},
+                             {3597813, -11584896, 14319786, -8079576, 1746873},
+                             {-2004757, 6499258, -8079576, 4577926, -992851},
+                             {429679, -1399537, 1746873, -992851, 215836}};
+    double v;
+    if (k == 0) v = B0[a][b];
+    else if (k == 1) v = B1[a][b];
+    else if (k == 2) v = B2[a][b];
+    else if (k == 3) v = B1[4 - a][4 - b];
+    else if (k == 4) v = B0[4 - a][4 - b];
+    else v = Bd[a][b];
+    return v / 10080.0;
+  }
+  __device__ static double ctau(int j) {
+    const double v[10] = {-1, 9, -36, 84, -126, 126, -84, 36, -9, 1};
+    return v[j];
+  }
+};
+
+template <int R, bool AI, bool P1>
+__device__ __forceinline__ double za_r(const double (&v)[2 * R], const ReconParams &P) {
+  using Tb = OrderTab<R>;
+  constexpr int N = 2 * R;
+  const double vc = v[R - 1];
+  double beta[R + 1];
+  double bsum = 0.0;
+#pragma unroll
+  for (int k = 0; k <= R; ++k) {  // k = R: the downwind polynomial's beta_d
+    double g[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) g[m] = v[k + m] - v[k];
+    double s = 0.0;
+#pragma unroll
+    for (int a = 1; a < R; ++a) {
+      double row = 0.0;
+#pragma unroll
+      for (int b = 1; b < R; ++b) row = fma(Tb::B(k, a, b), g[b], row);
+      s = fma(g[a], row, s);
+    }
+    s = fmax(s, 0.0);
+    if (k < R) beta[k] = s;
+    bsum += s;
+  }
+  beta[R] = bsum * (1.0 / (R + 1));
+  double mean = 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) mean += v[j] - vc;
+  mean *= (1.0 / N);
+  double tr = 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) tr = fma(Tb::ctau(j), (v[j] - vc) - mean, tr);
+  const double tau = tr * tr;
+  double e;
+  if (AI) {
+    double dev = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) dev += fabs((v[j] - vc) - mean);
+    const double mu = fma(dev, 1.0 / N, P.mu0s);
+    e = 0.25 * P.eps4 * (mu * mu);
+  } else {
+    e = 0.25 * P.efix;
+  }
+  double asum = 0.0, num = 0.0;
+#pragma unroll
+  for (int k = 0; k <= R; ++k) {
+    double G = tau / (beta[k] + e);
+    if (!P1) G = pow(G, P.p);
+    const double al = Tb::d(k) * (1.0 + G);
+    double corr = 0.0;  // f^k - v_{R-1}
+#pragma unroll
+    for (int m = 0; m < R; ++m) corr = fma(Tb::ck(k, m), v[k + m] - vc, corr);
+    asum += al;
+    num = fma(al, corr, num);
+  }
+  return vc + num / asum;
+}
+
+// ---------------------------------------------------------------------------
 // FP32 reconstruction (precision mode WENO_PREC_FP32_RECON).
 //
 // Input: the five FP64 stencil differences d_j = v_{j+1} - v_j already

@@ -266,8 +266,10 @@ weno_status weno_engine_admit(weno_engine *E, const weno_desc *d, const double *
   if (!E || !d || !U_host || !slot_out) return efail(WENO_ERR_ARG, "NULL argument");
   *slot_out = -1;
   if (weno_workspace_bytes(d) == 0) return WENO_ERR_ARG;
-  if (d->system != WENO_SYS_EULER || d->nbatch != 1 || d->ai != 1 || d->p != 1.0)
-    return efail(WENO_ERR_ARG, "the engine serves single Euler problems with ai = 1, p = 1");
+  if (d->system != WENO_SYS_EULER || d->nbatch != 1 || d->ai != 1 || d->p != 1.0 ||
+      (d->order != 0 && d->order != 6))
+    return efail(WENO_ERR_ARG,
+                 "the engine serves single sixth-order Euler problems with ai = 1, p = 1");
   if (!(std::isfinite(t_final) && t_final > 0.0)) return efail(WENO_ERR_ARG, "t_final must be > 0");
   int k = -1;
   for (int q = 0; q < E->max_slots; ++q)

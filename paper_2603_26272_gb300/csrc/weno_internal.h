@@ -25,6 +25,7 @@ struct StageArgs {
   double cfl, eps, mu0, p;
   int ai, alpha_single;
   int precision;      // 0 FP64, 1 FP32 reconstruction
+  int order_r;        // r: stencil half-width, scheme order 2r (3 = WENO-ZA6)
   double ustar;       // Buckley-Leverett: maximiser of f' on [0, 1]
   int tile_variant;   // 2D tile shape: 0 32x16, 1 16x16, 2 16x8 (results identical)
   double adv_speed;
@@ -95,6 +96,8 @@ cudaError_t launch_engine_stage(const EngineArgs &e, int grid, cudaStream_t s);
 
 cudaError_t launch_alpha(const AlphaArgs &a, cudaStream_t s);
 cudaError_t launch_stage(const StageArgs &a, cudaStream_t s);
+// The same for a.order_r = 2, 4, 5 (FP64 reconstruction only).
+cudaError_t launch_stage_orders(const StageArgs &a, cudaStream_t s);
 // alpha bits -> doubles, and the CFL dt per problem
 cudaError_t launch_alpha_export(const AlphaArgs &a, const unsigned long long *bits, double *alpha,
                                 double *dt, cudaStream_t s);

@@ -1,564 +1,12 @@
-// weno_kernels.cu -- CUDA kernels of the WENO-ZA6 right-hand side and the
-// SSP-RK3 stage update for GB300 (sm_103a).
-//
-// One launch = one Runge-Kutta stage over every problem of the batch
-// (Section 4 preamble: third-order TVD Runge-Kutta).  A block owns a tile of
-// cells and runs three phases:
-//   1. stage the tile and its 3-cell halo (the 6-point stencil S^6 of
-//      eq. (7)) into shared memory, with ghost cells by index clamp or wrap,
-//      and form per-cell primitives and physical fluxes once;
-//   2. compute every interface flux of the tile exactly once -- in 2D the x-
-//      and y-faces of one tile come from the same staged data (dimension by
-//      dimension, Section 4.3) -- by characteristic-wise global
-//      Lax-Friedrichs splitting (eq. (6), Section 4.2) and WENO-ZA6
-//      (Section 3) for the positive and the mirrored negative flux;
-//   3. per cell, the conservative difference of eq. (5), the Runge-Kutta
-//      combination, and -- for the next stage -- the block's maxima of the
-//      characteristic speeds, reduced with warp shuffles and one atomicMax
-//      per value and block.
-#include <cfloat>
-#include <cmath>
-
-#include "weno_device.cuh"
-#include "weno_internal.h"
+// weno_kernels.cu -- sixth-order (WENO-ZA6) stage launches, the wavespeed
+// reductions of eq. (6), the serving engine's persistent stage kernel and the
+// host-side launchers for GB300 (sm_103a).  The tile kernels themselves are in
+// weno_tiles.cuh; the schemes of other orders are instantiated in
+// weno_orders.cu.
+#include "weno_tiles.cuh"
 
 namespace weno {
 namespace {
-
-constexpr int kThreads2D = 256;
-constexpr int kTX = 32, kTY = 16;
-constexpr int kThreads1D = 128;
-constexpr int kT1 = kThreads1D - 1;  // cells per 1D tile: one face per thread
-
-__device__ __forceinline__ long long ghost(long long k, long long n, int bc) {
-  if (bc == 1) {
-    long long m = k % n;
-    return m < 0 ? m + n : m;
-  }
-  return k < 0 ? 0 : (k >= n ? n - 1 : k);
-}
-
-__device__ __forceinline__ double bits2d(unsigned long long u) {
-  return __longlong_as_double((long long)u);
-}
-
-__device__ void record_status(DevStatus *st, int code, int stage, long long b, long long j,
-                              long long i) {
-  if (atomicCAS(&st->code, 0, code) == 0) {
-    st->stage = stage;
-    st->b = b;
-    st->j = j;
-    st->i = i;
-  }
-}
-
-// CFL step of problem b from its speed maxima (bit patterns), the rule of
-// the oracle: 1D cfl dx / max(|u|+c); 2D cfl / (max(|u|+c)/dx + max(|v|+c)/dy).
-// max(|u-c|, |u+c|) = |u| + c exactly (same rounding).
-// Scalar systems 2, 3 keep okey(max u) and okey(max -u) in slots 0 and 1.
-__device__ __forceinline__ double scalar_alpha_of(int system, double adv, double ustar,
-                                                  const unsigned long long *al) {
-  if (system == 0) return fabs(adv);
-  const double umax = okey_inv(al[0]), umin = -okey_inv(al[1]);
-  return scalar_alpha(system, adv, umin, umax, ustar);
-}
-
-__device__ double cfl_dt(int system, int ndim, int nc, double cfl, double dx, double dy,
-                         double adv, const unsigned long long *al, double ustar = 0.0) {
-  if (system == 0) return cfl * dx / fabs(adv);
-  if (system >= 2) return cfl * dx / scalar_alpha_of(system, adv, ustar, al);
-  const unsigned long long sxb = max(al[0], al[nc == 3 ? 2 : 3]);
-  const double sx = bits2d(sxb);
-  if (ndim == 1) return cfl * dx / sx;
-  const double sy = bits2d(max(al[4], al[7]));
-  return cfl / (sx / dx + sy / dy);
-}
-
-// Block-level control shared by every stage kernel: clears the slot of the
-// stage after next, decides this problem's dt, advances its clock.
-// Returns false if the block has nothing to do.
-__device__ bool stage_control(const StageArgs &a, long long b, bool first_block_of_b,
-                              bool zeroing_block, double &dt_out) {
-  __shared__ double s_dt;
-  __shared__ int s_go;
-  if (a.alpha_zero && zeroing_block)
-    for (long long k = threadIdx.x; k < a.nbatch * 8; k += blockDim.x) a.alpha_zero[k] = 0ull;
-  if (threadIdx.x == 0) {
-    int go = 1;
-    double dt = 0.0;
-    if (*(volatile int *)&a.status->code != 0) {
-      go = 0;
-    } else if (a.mode == 0) {
-      if (a.stage == 1) {
-        const double t = a.t[b];
-        if (!(t < a.t_final)) {
-          go = 0;
-          if (first_block_of_b) a.dt[b] = 0.0;
-        } else {
-          dt = a.dt_fixed > 0.0 ? a.dt_fixed
-                                : cfl_dt(a.system, a.ndim, a.nc, a.cfl, a.dx, a.dy,
-                                         a.adv_speed, a.alpha_in + b * 8, a.ustar);
-          const double rem = a.t_final - t;
-          const bool last = !(dt < rem);
-          if (last) dt = rem;
-          if (first_block_of_b) {
-            a.dt[b] = dt;
-            a.tnext[b] = last ? a.t_final : t + dt;
-          }
-        }
-      } else {
-        dt = a.dt[b];
-        if (dt == 0.0) go = 0;
-        if (go && a.stage == 3 && first_block_of_b) {
-          a.t[b] = a.tnext[b];
-          a.steps[b] += 1;
-        }
-      }
-    }
-    s_dt = dt;
-    s_go = go;
-  }
-  __syncthreads();
-  dt_out = s_dt;
-  return s_go != 0;
-}
-
-// Per-field reconstruction parameters; field m arrives scaled by k[m].
-__device__ __forceinline__ ReconParams make_rp(const StageArgs &a, double k) {
-  ReconParams r;
-  r.eps4 = 4.0 * a.eps;
-  r.mu0s = k * a.mu0;
-  r.efix = 4.0 * a.eps * k * k;
-  r.p = a.p;
-  return r;
-}
-
-__device__ __forceinline__ Recon32 make_r32(const StageArgs &a) {
-  Recon32 r;
-  r.eps4 = 4.0e-30f;
-  r.p = (float)a.p;
-  return r;
-}
-
-// Block reduction of NV maxima (bit patterns) and one atomicMax per value into
-// dst[slot[q]], and also into dst[dup[q]] where dup[q] >= 0 (the entropy and
-// shear fields share the speed |u|).
-template <int NV>
-__device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long *dst,
-                                 const int (&slot)[NV], const int (&dup)[NV]) {
-  __shared__ unsigned long long red[32][NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] = max(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) red[warp][q] = v[q];
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    unsigned long long m = 0;
-    for (int w = 0; w < nw; ++w) m = max(m, red[w][threadIdx.x]);
-    atomicMax(dst + slot[threadIdx.x], m);
-    if (dup[threadIdx.x] >= 0) atomicMax(dst + dup[threadIdx.x], m);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// 2D Euler stage kernel.
-// Shared planes per staged cell: 0 rho, 1 rho u, 2 rho v, 3 E, 4 u, 5 v, 6 H,
-// 7 sqrt(rho), 8-11 F (x flux), 12-15 G (y flux).
-// ---------------------------------------------------------------------------
-// One tile (tile index `tile` of problem b) of a 2D stage, run by one block.
-// sm: dynamic shared memory of smem_euler2d<TX, TY>() bytes.
-template <int TX, int TY>
-constexpr size_t smem_euler2d() {
-  return sizeof(double) * (16 * (TX + 6) * (TY + 6) + 4 * ((TX + 1) * TY + TX * (TY + 1)));
-}
-
-template <int TX, int TY, bool AI, bool P1, int PREC>
-__device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, long long tile,
-                                             bool zeroing_block, double *sm) {
-  constexpr int W = TX + 6, HH = TY + 6, REG = W * HH;
-  constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-  double *const pl = sm;
-  double *const fx = sm + 16 * REG;
-  double *const fy = fx + NFX * 4;
-
-  const long long tiles_x = (a.nx + TX - 1) / TX;
-  const long long tj = tile / tiles_x, ti = tile - tj * tiles_x;
-  const long long i0 = ti * TX, j0 = tj * TY;
-  double dt;
-  if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
-
-  const long long plane = a.nx * a.ny;
-  const double *Ub = a.Uin + b * 4 * plane;
-  const double gm1 = a.gamma - 1.0;
-  const int tid = threadIdx.x;
-
-  // Phase 1: stage the cross-shaped region (tile rows with x halo, tile
-  // columns with y halo) and per-cell primitives / fluxes.
-  for (int k = tid; k < REG; k += blockDim.x) {
-    const int r = k / W, c = k - r * W;
-    const bool xb = (r >= 3) && (r < 3 + TY), yb = (c >= 3) && (c < 3 + TX);
-    if (!(xb || yb)) continue;
-    const long long gi = ghost(i0 - 3 + c, a.nx, a.bc_x);
-    const long long gj = ghost(j0 - 3 + r, a.ny, a.bc_y);
-    const long long o = gj * a.nx + gi;
-    const double rho = Ub[o], mx = Ub[plane + o], my = Ub[2 * plane + o], E = Ub[3 * plane + o];
-    const double rs = rsqrt(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
-    const double ir = rs * rs;
-    const double u = mx * ir, v = my * ir;
-    const double p = gm1 * (E - 0.5 * fma(mx, u, my * v));
-    if (!(pos_finite(rho) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
-    const double rH = E + p;
-    const double ruv = my * u;
-    pl[0 * REG + k] = rho;
-    pl[1 * REG + k] = mx;
-    pl[2 * REG + k] = my;
-    pl[3 * REG + k] = E;
-    pl[4 * REG + k] = u;
-    pl[5 * REG + k] = v;
-    pl[6 * REG + k] = rH * ir;
-    pl[7 * REG + k] = rho * rs;
-    pl[8 * REG + k] = mx;
-    pl[9 * REG + k] = fma(mx, u, p);
-    pl[10 * REG + k] = ruv;
-    pl[11 * REG + k] = rH * u;
-    pl[12 * REG + k] = my;
-    pl[13 * REG + k] = ruv;
-    pl[14 * REG + k] = fma(my, v, p);
-    pl[15 * REG + k] = rH * v;
-  }
-  __syncthreads();
-
-  // Phase 2: every x- and y-face of the tile once.  Lanes of a warp may mix
-  // directions; the code path is the same (only the plane indices differ).
-  const unsigned long long *al = a.alpha_in + b * 8;
-  const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
-  for (int f = tid; f < NFX + NFY; f += blockDim.x) {
-    int base, stride, dir, fr, fc;
-    if (f < NFX) {
-      fr = f / (TX + 1);
-      fc = f - fr * (TX + 1);
-      base = (3 + fr) * W + fc;
-      stride = 1;
-      dir = 0;
-    } else {
-      const int g = f - NFX;
-      fr = g / TX;
-      fc = g - fr * TX;
-      base = fr * W + 3 + fc;
-      stride = W;
-      dir = 1;
-    }
-    const int pmn = 1 + dir, pmt = 2 - dir, pun = 4 + dir, put = 5 - dir;
-    const int pf0 = 8 + 4 * dir, pf1 = 9 + 5 * dir, pf2 = 10 + 3 * dir, pf3 = 11 + 4 * dir;
-    const int kL = base + 2 * stride, kR = base + 3 * stride;
-    FaceState fs;
-    if (!roe_face(pl[7 * REG + kL], pl[pun * REG + kL], pl[put * REG + kL], pl[6 * REG + kL],
-                  pl[7 * REG + kR], pl[pun * REG + kR], pl[put * REG + kR], pl[6 * REG + kR],
-                  gm1, fs))
-      record_status(a.status, 3, a.stage, b, j0 + (dir ? fr : fr), i0 + fc);
-    double A1 = bits2d(al[4 * dir + 0]), A2 = bits2d(al[4 * dir + 1]);
-    double A3 = bits2d(al[4 * dir + 2]), A4 = bits2d(al[4 * dir + 3]);
-    if (a.alpha_single) {
-      const double m = fmax(fmax(A1, A2), fmax(A3, A4));
-      A1 = A2 = A3 = A4 = m;
-    }
-    double h1, h2, h3, h4;
-    if (PREC == 1) {
-      // FP32 reconstruction: FP64 projections, FP32 split and WENO-ZA6.
-      double W[4][6], G[4][6];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int k = base + j * stride;
-        project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], W[0][j],
-                 W[1][j], W[2][j], W[3][j]);
-        project4(fs, pl[pf0 * REG + k], pl[pf1 * REG + k], pl[pf2 * REG + k], pl[pf3 * REG + k],
-                 G[0][j], G[1][j], G[2][j], G[3][j]);
-      }
-      const Recon32 r32 = make_r32(a);
-      h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
-      h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
-      h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
-      h4 = field_flux_f32<P1>(W[3], G[3], A4, r32);
-    } else {
-      double p1[6], p2[6], p3[6], p4[6], m1[6], m2[6], m3[6], m4[6];
-  #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int k = base + j * stride;
-        double w1, w2, w3, w4, g1, g2, g3, g4;
-        project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], w1, w2, w3, w4);
-        project4(fs, pl[pf0 * REG + k], pl[pf1 * REG + k], pl[pf2 * REG + k], pl[pf3 * REG + k],
-                 g1, g2, g3, g4);
-        p1[j] = fma(A1, w1, g1);
-        m1[j] = fma(-A1, w1, g1);
-        p2[j] = fma(A2, w2, g2);
-        m2[j] = fma(-A2, w2, g2);
-        p3[j] = fma(A3, w3, g3);
-        m3[j] = fma(-A3, w3, g3);
-        p4[j] = fma(A4, w4, g4);
-        m4[j] = fma(-A4, w4, g4);
-      }
-      h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
-                        za6<AI, P1>(m1[5], m1[4], m1[3], m1[2], m1[1], m1[0], rp4);
-      h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
-                        za6<AI, P1>(m2[5], m2[4], m2[3], m2[2], m2[1], m2[0], rp2);
-      h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp2) +
-                        za6<AI, P1>(m3[5], m3[4], m3[3], m3[2], m3[1], m3[0], rp2);
-      h4 = za6<AI, P1>(p4[0], p4[1], p4[2], p4[3], p4[4], p4[5], rp4) +
-                        za6<AI, P1>(m4[5], m4[4], m4[3], m4[2], m4[1], m4[0], rp4);
-  }
-    double F0, F1, F2, F3;
-    backproject4(fs, h1, h2, h3, h4, F0, F1, F2, F3);
-    double *out = dir ? &fy[(fr * TX + fc) * 4] : &fx[(fr * (TX + 1) + fc) * 4];
-    out[0] = F0;
-    out[1 + dir] = F1;
-    out[2 - dir] = F2;
-    out[3] = F3;
-  }
-  __syncthreads();
-
-  // Phase 3: conservative difference, RK combination, next-stage speeds.
-  const double idx = 1.0 / a.dx, idy = 1.0 / a.dy;
-  unsigned long long mx6[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-  const bool want_alpha = (a.mode == 0) && (a.alpha_out != nullptr);
-  for (int k = tid; k < TX * TY; k += blockDim.x) {
-    const int r = k / TX, c = k - r * TX;
-    const long long gi = i0 + c, gj = j0 + r;
-    if (gi >= a.nx || gj >= a.ny) continue;
-    const double *Fl = &fx[(r * (TX + 1) + c) * 4];
-    const double *Fr = Fl + 4;
-    const double *Gb = &fy[(r * TX + c) * 4];
-    const double *Gt = &fy[((r + 1) * TX + c) * 4];
-    const int kc = (3 + r) * W + 3 + c;
-    const long long o = b * 4 * plane + gj * a.nx + gi;
-    double uo[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double L = -(Fr[q] - Fl[q]) * idx - (Gt[q] - Gb[q]) * idy;
-      if (a.mode == 1) {
-        uo[q] = L;
-      } else {
-        const double base_s = fma(dt, L, pl[q * REG + kc]);
-        uo[q] = (a.a_n != 0.0) ? fma(a.a_n, a.Un[o + q * plane], a.a_s * base_s) : a.a_s * base_s;
-      }
-      a.Uout[o + q * plane] = uo[q];
-    }
-    if (want_alpha) {
-      const double ir = 1.0 / uo[0];
-      const double u = uo[1] * ir, v = uo[2] * ir;
-      const double p = gm1 * (uo[3] - 0.5 * fma(uo[1], u, uo[2] * v));
-      if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
-      const double cs = sqrt(a.gamma * p * ir);
-      mx6[0] = max(mx6[0], abs_bits(u - cs));
-      mx6[1] = max(mx6[1], abs_bits(u));
-      mx6[2] = max(mx6[2], abs_bits(u + cs));
-      mx6[3] = max(mx6[3], abs_bits(v - cs));
-      mx6[4] = max(mx6[4], abs_bits(v));
-      mx6[5] = max(mx6[5], abs_bits(v + cs));
-    }
-  }
-  if (want_alpha) {
-    const int slot[6] = {0, 1, 3, 4, 5, 7};
-    const int dup[6] = {-1, 2, -1, -1, 6, -1};
-    block_max_atomic<6>(mx6, a.alpha_out + b * 8, slot, dup);
-  }
-}
-
-template <int TX, int TY, int NT, bool AI, bool P1, int PREC>
-__global__ void __launch_bounds__(NT, (NT >= 256 ? 1 : 256 / NT)) k_euler2d(const StageArgs a) {
-  extern __shared__ double sm[];
-  euler2d_tile<TX, TY, AI, P1, PREC>(a, blockIdx.z, blockIdx.x,
-                                     blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
-}
-
-// ---------------------------------------------------------------------------
-// 1D stage kernel: NC = 3 (Euler) or 1 (scalar advection).  Tile of
-// kT1 = 127 cells, 128 faces, one face per thread.
-// Planes: 0 rho, 1 m, 2 E, 3 u, 4 H, 5 sqrt(rho), 6-8 F  (advection: 0 u).
-// ---------------------------------------------------------------------------
-template <int NC, int T>
-constexpr size_t smem_line1d() {
-  return sizeof(double) * (((NC == 3) ? 9 : 2) * (T + 6) + (T + 1) * NC);
-}
-
-// One tile of T cells (T + 1 faces, one per thread; blockDim = T + 1) of a
-// 1D stage.  sm: dynamic shared memory of smem_line1d<NC, T>() bytes.
-template <int NC, bool AI, bool P1, int PREC, int T>
-__device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, long long tile,
-                                            bool zeroing_block, double *sm) {
-  constexpr int REG = T + 6;
-  constexpr int NP = (NC == 3) ? 9 : 2;
-  double(*pl)[REG] = reinterpret_cast<double(*)[REG]>(sm);
-  double(*fl)[NC] = reinterpret_cast<double(*)[NC]>(sm + NP * REG);
-  const long long i0 = tile * T;
-  double dt;
-  if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
-  const long long nx = a.nx;
-  const double *Ub = a.Uin + b * NC * nx;
-  const double gm1 = a.gamma - 1.0;
-  const int tid = threadIdx.x;
-
-  for (int k = tid; k < REG; k += blockDim.x) {
-    const long long gi = ghost(i0 - 3 + k, nx, a.bc_x);
-    if (NC == 1) {
-      const double u = Ub[gi];
-      if (!(u == u) || fabs(u) > 1.7e308) record_status(a.status, 3, a.stage, b, 0, gi);
-      pl[0][k] = u;
-      pl[1][k] = scalar_flux(a.system, a.adv_speed, u);
-    } else {
-      const double rho = Ub[gi], m = Ub[nx + gi], E = Ub[2 * nx + gi];
-      const double rs = rsqrt(rho);
-      const double ir = rs * rs;
-      const double u = m * ir;
-      const double p = gm1 * (E - 0.5 * (m * u));
-      if (!(pos_finite(rho) && pos_finite(p))) record_status(a.status, 3, a.stage, b, 0, gi);
-      const double rH = E + p;
-      pl[0][k] = rho;
-      pl[1][k] = m;
-      pl[2][k] = E;
-      pl[3][k] = u;
-      pl[4][k] = rH * ir;
-      pl[5][k] = rho * rs;
-      pl[6][k] = m;
-      pl[7][k] = fma(m, u, p);
-      pl[8][k] = rH * u;
-    }
-  }
-  __syncthreads();
-
-  {
-    const int f = tid;  // face between cells i0+f-1 and i0+f; stencil cells f..f+5
-    if (f <= T && i0 + f - 1 < nx) {
-      if (NC == 1) {
-        const double A = scalar_alpha_of(a.system, a.adv_speed, a.ustar, a.alpha_in + b * 8);
-        double h;
-        if (PREC == 1) {
-          double w[6], g[6];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            w[j] = pl[0][f + j];
-            g[j] = pl[1][f + j];
-          }
-          h = field_flux_f32<P1>(w, g, A, make_r32(a));
-        } else {
-          const ReconParams rp = make_rp(a, 2.0);
-          double pp[6], mm[6];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            const double v = pl[0][f + j], fv = pl[1][f + j];
-            pp[j] = fma(A, v, fv);
-            mm[j] = fma(-A, v, fv);
-          }
-          h = za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp) +
-              za6<AI, P1>(mm[5], mm[4], mm[3], mm[2], mm[1], mm[0], rp);
-        }
-        fl[f][0] = 0.5 * h;
-      } else {
-        const int kL = f + 2, kR = f + 3;
-        FaceState fs;
-        if (!roe_face(pl[5][kL], pl[3][kL], 0.0, pl[4][kL], pl[5][kR], pl[3][kR], 0.0, pl[4][kR],
-                      gm1, fs))
-          record_status(a.status, 3, a.stage, b, 0, i0 + f);
-        const unsigned long long *al = a.alpha_in + b * 8;
-        double A1 = bits2d(al[0]), A2 = bits2d(al[1]), A3 = bits2d(al[2]);
-        if (a.alpha_single) A1 = A2 = A3 = fmax(fmax(A1, A2), A3);
-        double h1, h2, h3;
-        if (PREC == 1) {
-          double W[3][6], G[3][6];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            const int k = f + j;
-            project3(fs, pl[0][k], pl[1][k], pl[2][k], W[0][j], W[1][j], W[2][j]);
-            project3(fs, pl[6][k], pl[7][k], pl[8][k], G[0][j], G[1][j], G[2][j]);
-          }
-          const Recon32 r32 = make_r32(a);
-          h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
-          h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
-          h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
-        } else {
-          const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
-          double p1[6], p2[6], p3[6], m1[6], m2[6], m3[6];
-  #pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            const int k = f + j;
-            double w1, w2, w3, g1, g2, g3;
-            project3(fs, pl[0][k], pl[1][k], pl[2][k], w1, w2, w3);
-            project3(fs, pl[6][k], pl[7][k], pl[8][k], g1, g2, g3);
-            p1[j] = fma(A1, w1, g1);
-            m1[j] = fma(-A1, w1, g1);
-            p2[j] = fma(A2, w2, g2);
-            m2[j] = fma(-A2, w2, g2);
-            p3[j] = fma(A3, w3, g3);
-            m3[j] = fma(-A3, w3, g3);
-          }
-          h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
-                            za6<AI, P1>(m1[5], m1[4], m1[3], m1[2], m1[1], m1[0], rp4);
-          h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
-                            za6<AI, P1>(m2[5], m2[4], m2[3], m2[2], m2[1], m2[0], rp2);
-          h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp4) +
-                            za6<AI, P1>(m3[5], m3[4], m3[3], m3[2], m3[1], m3[0], rp4);
-  }
-        double F0, F1, F2;
-        backproject3(fs, h1, h2, h3, F0, F1, F2);
-        fl[f][0] = F0;
-        fl[f][1] = F1;
-        fl[f][2] = F2;
-      }
-    }
-  }
-  __syncthreads();
-
-  const double idx = 1.0 / a.dx;
-  unsigned long long m3v[3] = {0ull, 0ull, 0ull};
-  const bool want_alpha = (NC == 3 || a.system >= 2) && (a.mode == 0) && (a.alpha_out != nullptr);
-  if (tid < T && i0 + tid < nx) {
-    const long long gi = i0 + tid;
-    const long long o = b * NC * nx + gi;
-    double uo[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      const double L = -(fl[tid + 1][q] - fl[tid][q]) * idx;
-      if (a.mode == 1) {
-        uo[q] = L;
-      } else {
-        const double uin = (NC == 1) ? pl[0][tid + 3] : pl[q][tid + 3];
-        const double base_s = fma(dt, L, uin);
-        uo[q] = (a.a_n != 0.0) ? fma(a.a_n, a.Un[o + q * nx], a.a_s * base_s) : a.a_s * base_s;
-      }
-      a.Uout[o + q * nx] = uo[q];
-    }
-    if (want_alpha && NC == 1) {  // scalar: keys of max u and max -u
-      if (!(uo[0] == uo[0]) || fabs(uo[0]) > 1.7e308) record_status(a.status, 3, a.stage, b, 0, gi);
-      m3v[0] = okey(uo[0]);
-      m3v[1] = okey(-uo[0]);
-    } else if (want_alpha) {
-      const double ir = 1.0 / uo[0];
-      const double u = uo[1] * ir;
-      const double p = gm1 * (uo[NC - 1] - 0.5 * (uo[1] * u));
-      if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, 0, gi);
-      const double cs = sqrt(a.gamma * p * ir);
-      m3v[0] = abs_bits(u - cs);
-      m3v[1] = abs_bits(u);
-      m3v[2] = abs_bits(u + cs);
-    }
-  }
-  if (want_alpha) {
-    const int slot[3] = {0, 1, 2};
-    const int dup[3] = {-1, -1, -1};
-    block_max_atomic<3>(m3v, a.alpha_out + b * 8, slot, dup);
-  }
-}
-
-template <int NC, bool AI, bool P1, int PREC>
-__global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
-  extern __shared__ double sm[];
-  line1d_tile<NC, AI, P1, PREC, kT1>(a, blockIdx.y, blockIdx.x,
-                                     blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
-}
 
 // ---------------------------------------------------------------------------
 // Wavespeed maxima of a state (the GLF speeds of eq. (6)), grid-stride per
@@ -729,44 +177,20 @@ __global__ void __launch_bounds__(kEngineThreads, kEngineBlocksPerSM) k_engine(c
   }
 }
 
-template <int TX, int TY, int NT, bool AI, bool P1, int PREC>
-cudaError_t launch_2d(const StageArgs &a, cudaStream_t s) {
-  const size_t smem = smem_euler2d<TX, TY>();
-  auto kern = k_euler2d<TX, TY, NT, AI, P1, PREC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const long long tiles = ((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
-  dim3 grid((unsigned)tiles, 1, (unsigned)a.nbatch);
-  kern<<<grid, NT, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <bool AI, bool P1, int PREC>
-cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
-  if (a.ndim == 2) {
-    // tile variants: 0 = 32x16 cells / 256 threads (fewest halo faces),
-    // 1 = 16x16 / 128, 2 = 16x8 / 64 (more tiles for small grids)
-    if (a.tile_variant == 1) return launch_2d<16, 16, 128, AI, P1, PREC>(a, s);
-    if (a.tile_variant == 2) return launch_2d<16, 8, 64, AI, P1, PREC>(a, s);
-    return launch_2d<kTX, kTY, kThreads2D, AI, P1, PREC>(a, s);
-  }
-  const long long tiles = (a.nx + kT1 - 1) / kT1;
-  dim3 grid((unsigned)tiles, (unsigned)a.nbatch, 1);
-  if (a.nc == 3)
-    k_line1d<3, AI, P1, PREC><<<grid, kThreads1D, smem_line1d<3, kT1>(), s>>>(a);
-  else
-    k_line1d<1, AI, P1, PREC><<<grid, kThreads1D, smem_line1d<1, kT1>(), s>>>(a);
-  return cudaGetLastError();
+template <bool AI, bool P1>
+cudaError_t launch_order(const StageArgs &a, cudaStream_t s) {
+  if (a.order_r != 3) return launch_stage_orders(a, s);  // weno_orders.cu
+  return launch_stage_t<AI, P1, 0, 3>(a, s);
 }
 
 }  // namespace
 
 cudaError_t launch_stage(const StageArgs &a, cudaStream_t s) {
   const bool p1 = (a.p == 1.0);
-  if (a.precision == 1)  // FP32 reconstruction (affine-invariant weights only)
-    return p1 ? launch_stage_t<true, true, 1>(a, s) : launch_stage_t<true, false, 1>(a, s);
-  if (a.ai) return p1 ? launch_stage_t<true, true, 0>(a, s) : launch_stage_t<true, false, 0>(a, s);
-  return p1 ? launch_stage_t<false, true, 0>(a, s) : launch_stage_t<false, false, 0>(a, s);
+  if (a.precision == 1)  // FP32 reconstruction (affine-invariant weights, order 6)
+    return p1 ? launch_stage_t<true, true, 1, 3>(a, s) : launch_stage_t<true, false, 1, 3>(a, s);
+  if (a.ai) return p1 ? launch_order<true, true>(a, s) : launch_order<true, false>(a, s);
+  return p1 ? launch_order<false, true>(a, s) : launch_order<false, false>(a, s);
 }
 
 size_t engine_smem_bytes() {

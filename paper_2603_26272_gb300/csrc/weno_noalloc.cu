@@ -128,6 +128,7 @@ extern "C" weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, dou
   r.ai = d->ai;
   r.alpha_single = d->alpha_mode == WENO_ALPHA_SINGLE;
   r.precision = d->precision;
+  r.order_r = d->order == 0 ? 3 : d->order / 2;
   r.ustar = weno::bl_speed_argmax();
   r.adv_speed = d->adv_speed;
   r.Uin = U;

@@ -47,7 +47,7 @@ class Desc(ctypes.Structure):
         ("ai", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("alpha_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("order", ctypes.c_int32),
         ("adv_speed", ctypes.c_double),
     ]
 
@@ -113,7 +113,8 @@ def _check(code):
 
 def make_desc(system="euler", ndim=1, nbatch=1, nx=1, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
               bc_x="transmissive", bc_y="transmissive", gamma=1.4, cfl=0.5, eps=1e-40,
-              mu0=1e-40, p=1.0, ai=True, precision="fp64", alpha_mode="field", adv_speed=1.0):
+              mu0=1e-40, p=1.0, ai=True, precision="fp64", alpha_mode="field", adv_speed=1.0,
+              order=6):
     d = Desc()
     d.system = SYSTEMS[system]
     d.ndim = ndim
@@ -131,7 +132,7 @@ def make_desc(system="euler", ndim=1, nbatch=1, nx=1, ny=1, x0=0.0, x1=1.0, y0=0
     d.ai = int(bool(ai))
     d.precision = PRECISIONS[precision]
     d.alpha_mode = ALPHA_MODES[alpha_mode]
-    d.reserved = 0
+    d.order = int(order)
     d.adv_speed = adv_speed
     return d
 

@@ -35,6 +35,11 @@ def test_descriptor_layout_matches_header():
     # the header's field order and types, as ctypes lays them out (C rules)
     assert ctypes.sizeof(weno.Desc) == 136
     assert weno.Desc.adv_speed.offset == 128
+    src = open(os.path.join(ROOT, "include", "weno.h")).read()
+    body = src[src.index("typedef struct weno_desc"):src.index("} weno_desc;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b([a-z_0-9]+)\s*[;,]", body)
+    assert names == [f[0] for f in weno.Desc._fields_]
 
 
 def test_workspace_bytes_and_argument_checks(L):
@@ -45,13 +50,20 @@ def test_workspace_bytes_and_argument_checks(L):
     assert weno.workspace_bytes(d, host=True) >= n + state
     bad = [dict(ndim=3), dict(nx=0), dict(ndim=1, ny=2), dict(gamma=1.0), dict(cfl=0.0),
            dict(eps=0.0), dict(precision="fp32_recon", ai=False), dict(system="advection", ndim=2, ny=4),
-           dict(nbatch=70000), dict(x1=0.0)]
+           dict(nbatch=70000), dict(x1=0.0), dict(order=5), dict(order=12), dict(order=2),
+           dict(order=8, precision="fp32_recon")]
     for kw in bad:
         args = dict(system="euler", ndim=2, nx=8, ny=8)
         args.update(kw)
         d = weno.make_desc(**args)
         assert L.weno_workspace_bytes(ctypes.byref(d)) == 0, kw
         assert L.weno_last_error().decode() != ""
+
+
+def test_every_order_of_the_family_is_accepted(L):
+    for order in (0, 4, 6, 8, 10):
+        d = weno.make_desc(system="euler", ndim=2, nx=8, ny=8, order=order)
+        assert L.weno_workspace_bytes(ctypes.byref(d)) > 0, order
 
 
 def test_entry_points_reject_bad_arguments_before_any_device_work(L):
