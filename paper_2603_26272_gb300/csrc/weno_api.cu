@@ -283,7 +283,7 @@ int tile_override() {
   const char *v = std::getenv("WENO_TILE2D");
   if (!v || !*v) return -1;
   const int t = std::atoi(v);
-  return (t >= 0 && t <= 2) ? t : -1;
+  return (t >= 0 && t < weno::kTileVariants) ? t : -1;
 }
 
 weno_status choose_tile(const Ctx &c, const double *U, const unsigned long long *alpha, int *out) {
@@ -320,7 +320,7 @@ weno_status choose_tile(const Ctx &c, const double *U, const unsigned long long 
   int best = 0;
   float best_ms = 0.0f;
   weno_status st = WENO_OK;
-  for (int v = 0; v < 3 && st == WENO_OK; ++v) {
+  for (int v = 0; v < weno::kTileVariants && st == WENO_OK; ++v) {
     a.tile_variant = v;
     cudaError_t e = weno::launch_stage(a, c.s);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, c.s);

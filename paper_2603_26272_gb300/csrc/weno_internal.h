@@ -13,6 +13,9 @@ struct DevStatus {
   long long b, j, i;
 };
 
+// 2D tile variants of the single-problem stage kernel (see launch_stage_t).
+constexpr int kTileVariants = 5;
+
 // Everything one stage launch needs (passed by value).
 struct StageArgs {
   // grid
@@ -27,7 +30,7 @@ struct StageArgs {
   int precision;      // 0 FP64, 1 FP32 reconstruction
   int order_r;        // r: stencil half-width, scheme order 2r (3 = WENO-ZA6)
   double ustar;       // Buckley-Leverett: maximiser of f' on [0, 1]
-  int tile_variant;   // 2D tile shape: 0 32x16, 1 16x16, 2 16x8 (results identical)
+  int tile_variant;   // 2D tile shape, 0 .. kTileVariants-1 (results identical)
   double adv_speed;
   // data
   const double *Uin;  // stage input (read with the stencil)

@@ -174,15 +174,17 @@ __device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long
 // ---------------------------------------------------------------------------
 // 2D Euler stage kernel.
 // Shared planes per staged cell: 0 rho, 1 rho u, 2 rho v, 3 E, 4 u, 5 v, 6 H,
-// 7 sqrt(rho), 8-11 F (x flux), 12-15 G (y flux).
+// 7 sqrt(rho), 8 p (the fluxes are projected from u, v, p: project_flux4).
 // ---------------------------------------------------------------------------
 // One tile (tile index `tile` of problem b) of a 2D stage, run by one block.
 // R: half-width of the stencil (scheme of order 2R, halo of R cells).
 // sm: dynamic shared memory of smem_euler2d<TX, TY, R>() bytes.
+constexpr int kPlanes2D = 9;
+
 template <int TX, int TY, int R = 3>
 constexpr size_t smem_euler2d() {
   return sizeof(double) *
-         (16 * (TX + 2 * R) * (TY + 2 * R) + 4 * ((TX + 1) * TY + TX * (TY + 1)));
+         (kPlanes2D * (TX + 2 * R) * (TY + 2 * R) + 4 * ((TX + 1) * TY + TX * (TY + 1)));
 }
 
 template <int TX, int TY, bool AI, bool P1, int PREC, int R = 3>
@@ -192,7 +194,7 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
   constexpr int W = TX + 2 * R, HH = TY + 2 * R, REG = W * HH;
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
   double *const pl = sm;
-  double *const fx = sm + 16 * REG;
+  double *const fx = sm + kPlanes2D * REG;
   double *const fy = fx + NFX * 4;
 
   const long long tiles_x = (a.nx + TX - 1) / TX;
@@ -221,24 +223,15 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
     const double u = mx * ir, v = my * ir;
     const double p = gm1 * (E - 0.5 * fma(mx, u, my * v));
     if (!(pos_finite(rho) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
-    const double rH = E + p;
-    const double ruv = my * u;
     pl[0 * REG + k] = rho;
     pl[1 * REG + k] = mx;
     pl[2 * REG + k] = my;
     pl[3 * REG + k] = E;
     pl[4 * REG + k] = u;
     pl[5 * REG + k] = v;
-    pl[6 * REG + k] = rH * ir;
+    pl[6 * REG + k] = (E + p) * ir;
     pl[7 * REG + k] = rho * rs;
-    pl[8 * REG + k] = mx;
-    pl[9 * REG + k] = fma(mx, u, p);
-    pl[10 * REG + k] = ruv;
-    pl[11 * REG + k] = rH * u;
-    pl[12 * REG + k] = my;
-    pl[13 * REG + k] = ruv;
-    pl[14 * REG + k] = fma(my, v, p);
-    pl[15 * REG + k] = rH * v;
+    pl[8 * REG + k] = p;
   }
   __syncthreads();
 
@@ -263,7 +256,6 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       dir = 1;
     }
     const int pmn = 1 + dir, pmt = 2 - dir, pun = 4 + dir, put = 5 - dir;
-    const int pf0 = 8 + 4 * dir, pf1 = 9 + 5 * dir, pf2 = 10 + 3 * dir, pf3 = 11 + 4 * dir;
     const int kL = base + (R - 1) * stride, kR = base + R * stride;
     FaceState fs;
     if (!roe_face(pl[7 * REG + kL], pl[pun * REG + kL], pl[put * REG + kL], pl[6 * REG + kL],
@@ -285,8 +277,8 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
         const int k = base + j * stride;
         project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], W[0][j],
                  W[1][j], W[2][j], W[3][j]);
-        project4(fs, pl[pf0 * REG + k], pl[pf1 * REG + k], pl[pf2 * REG + k], pl[pf3 * REG + k],
-                 G[0][j], G[1][j], G[2][j], G[3][j]);
+        project_flux4(fs, pl[pun * REG + k], pl[8 * REG + k], W[0][j], W[1][j], W[2][j],
+                      W[3][j], G[0][j], G[1][j], G[2][j], G[3][j]);
       }
       const Recon32 r32 = make_r32(a);
       h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
@@ -302,8 +294,7 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
         const int k = base + j * stride;
         double w1, w2, w3, w4, g1, g2, g3, g4;
         project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], w1, w2, w3, w4);
-        project4(fs, pl[pf0 * REG + k], pl[pf1 * REG + k], pl[pf2 * REG + k], pl[pf3 * REG + k],
-                 g1, g2, g3, g4);
+        project_flux4(fs, pl[pun * REG + k], pl[8 * REG + k], w1, w2, w3, w4, g1, g2, g3, g4);
         p1[j] = fma(A1, w1, g1);
         m1[N - 1 - j] = fma(-A1, w1, g1);
         p2[j] = fma(A2, w2, g2);
@@ -386,8 +377,9 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
   }
 }
 
-template <int TX, int TY, int NT, bool AI, bool P1, int PREC, int R = 3>
-__global__ void __launch_bounds__(NT, (NT >= 256 ? 1 : 256 / NT)) k_euler2d(const StageArgs a) {
+// MINB: resident blocks per SM the register allocation must allow.
+template <int TX, int TY, int NT, int MINB, bool AI, bool P1, int PREC, int R = 3>
+__global__ void __launch_bounds__(NT, MINB) k_euler2d(const StageArgs a) {
   extern __shared__ double sm[];
   euler2d_tile<TX, TY, AI, P1, PREC, R>(a, blockIdx.z, blockIdx.x,
                                         blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
@@ -589,10 +581,10 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
                                         blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
 }
 
-template <int TX, int TY, int NT, bool AI, bool P1, int PREC, int R = 3>
+template <int TX, int TY, int NT, int MINB, bool AI, bool P1, int PREC, int R = 3>
 cudaError_t launch_2d(const StageArgs &a, cudaStream_t s) {
   const size_t smem = smem_euler2d<TX, TY, R>();
-  auto kern = k_euler2d<TX, TY, NT, AI, P1, PREC, R>;
+  auto kern = k_euler2d<TX, TY, NT, MINB, AI, P1, PREC, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = ((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
@@ -604,15 +596,21 @@ cudaError_t launch_2d(const StageArgs &a, cudaStream_t s) {
 template <bool AI, bool P1, int PREC, int R>
 cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
   if (a.ndim == 2) {
-    // tile variants: 0 = 32x16 cells / 256 threads (fewest halo faces),
-    // 1 = 16x16 / 128, 2 = 16x8 / 64 (more tiles for small grids).  The
-    // other orders use 16x16 / 128 only (their wider halo and stencil).
+    // tile variants (cells / threads / blocks per SM the registers allow):
+    // 0 = 32x16 / 256 / 1 (fewest halo faces), 1 = 16x16 / 128 / 2,
+    // 2 = 16x8 / 64 / 4 (more tiles for small grids), 3 = 16x16 / 128 / 3,
+    // 4 = 16x8 / 64 / 6.  The other orders use 16x16 / 128 / 2 only (their
+    // wider halo and stencil).
     if constexpr (R != 3) {
-      return launch_2d<16, 16, 128, AI, P1, PREC, R>(a, s);
+      return launch_2d<16, 16, 128, 2, AI, P1, PREC, R>(a, s);
     } else {
-      if (a.tile_variant == 1) return launch_2d<16, 16, 128, AI, P1, PREC>(a, s);
-      if (a.tile_variant == 2) return launch_2d<16, 8, 64, AI, P1, PREC>(a, s);
-      return launch_2d<kTX, kTY, kThreads2D, AI, P1, PREC>(a, s);
+      switch (a.tile_variant) {
+        case 1: return launch_2d<16, 16, 128, 2, AI, P1, PREC>(a, s);
+        case 2: return launch_2d<16, 8, 64, 4, AI, P1, PREC>(a, s);
+        case 3: return launch_2d<16, 16, 128, 3, AI, P1, PREC>(a, s);
+        case 4: return launch_2d<16, 8, 64, 6, AI, P1, PREC>(a, s);
+        default: return launch_2d<kTX, kTY, kThreads2D, 1, AI, P1, PREC>(a, s);
+      }
     }
   }
   const long long tiles = (a.nx + kT1 - 1) / kT1;

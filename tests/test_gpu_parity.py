@@ -318,14 +318,15 @@ def test_tile_variants_are_bitwise_identical(prec, monkeypatch):
     w["U"] = np.ascontiguousarray(w["U"][:, :, :53, :])
     d = _fix_2d_domain(w, weno.desc_for(w, precision=prec))
     outs = []
-    for v in ("0", "1", "2"):
+    for v in ("0", "1", "2", "3", "4"):
         monkeypatch.setenv("WENO_TILE2D", v)
         U = to_gpu(w["U"])
         for _ in range(3):
             weno.step(d, U)
         outs.append(U.cpu().numpy())
     monkeypatch.delenv("WENO_TILE2D")
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
     U = to_gpu(w["U"])  # the tuned choice (timed on first use) gives the same
     for _ in range(3):
         weno.step(d, U)
