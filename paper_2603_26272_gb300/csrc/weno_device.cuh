@@ -28,6 +28,8 @@ struct ReconParams {
   double mu0s;   // scale * mu_0       (Ai)
   double efix;   // 4 * eps * scale^2  (no Ai: mu = 1)
   double p;      // power parameter of eq. (21)
+  double me;     // sqrt(4 eps) / 6    (Ai: 4 eps mu^2 = (me * dev + mo)^2, dev =
+  double mo;     // sqrt(4 eps) * scale * mu_0   the sum of |v_j - mean v|)
 };
 
 // f > 0 and finite, by the bit pattern (integer pipe only).
@@ -95,39 +97,42 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 //   4 beta_3 = mean of the four (eq. (16)),
 //   4 tau = 4 (s3 - s0 + 3 (s1 - s2))^2 (eq. (17): the fifth difference),
 //   f^k = v2 + r_k / 6, r = (5d1 - 2d0, d1 + 2d2, 4d2 - d3, 6d2 - 5d3 + 2d4)
-//       (eq. (11)),
+//       = (2 t0 - d1, d1 + 2d2, 4d2 - d3, 6d2 + (t3 - d4))  (eq. (11)),
 //   mu = mean |v_j - mean v| + mu_0 (eq. (22)), Gamma_k = (tau/(beta_k +
 //   eps mu^2))^p (eq. (21)), alpha_k = d_k (1 + Gamma_k) (eq. (20), L = q = 1),
 //   f = sum alpha_k f^k / sum alpha_k (eqs. (14), (19)), d = (1, 9, 9, 1)/20.
 //
-// For p = 1 the four divisions tau/b_k are removed: with b_k = 4 beta_k +
-// 4 eps mu^2, alpha_k is proportional to d_k (b_k + 4 tau) prod_{j != k} b_j.
-// Before the products, b_k and 4 tau are multiplied by the power of two that
-// brings their maximum into [1, 2) (built from the exponent bits), so the
-// products can neither overflow nor underflow; one division remains.
+// The routine returns the parts v2, num = sum a_k r_k and den = sum a_k with
+// a_k proportional to alpha_k, so f = v2 + num / (6 den); pair_flux below
+// adds the positive and negative fluxes of a field with one division.
+// b_k = 4 beta_k + 4 eps mu^2 is formed as 13/3 s_k^2 + (t_k^2 + e), and
+// b_3 = mean of b_0, b_1, b_2, b_d (the same number as 4 beta_3 + e).
+//
+// For p = 1 the four divisions tau/b_k are removed: a_k = (b_k + 4 tau)
+// prod_{j != k} b_j (times d_k / d_0).  Before the products, the b_k and
+// 4 tau are multiplied by the power of two that brings their maximum into
+// [1, 2) (built from the exponent bits), so the products -- and the product
+// of two denominators in pair_flux -- can neither overflow nor underflow.
 //
 // mu is formed in FP32 from the FP64 differences: it enters only through
 // eps mu^2 with eps = 1e-40, which matters only for a substencil whose
 // indicator is below ~1e-30 mu^2, where a relative error of 1e-7 in mu moves
 // Gamma_k by the same relative amount and the weights by less than 1e-30.
 // ---------------------------------------------------------------------------
+struct ZA6Part {
+  double v2, num, den;  // f = v2 + num / (6 den)
+};
+
 template <bool AI, bool P1>
-__device__ __forceinline__ double za6(double v0, double v1, double v2, double v3, double v4,
-                                      double v5, const ReconParams &P) {
+__device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v3, double v4,
+                                       double v5, const ReconParams &P) {
   const double d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3, d4 = v5 - v4;
   const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
   const double t0 = fma(3.0, d1, -d0);
   const double t1 = d1 + d2;
   const double t2 = fma(3.0, d2, -d3);
   const double t3 = fma(3.0, d4, -5.0 * d3);
-  const double c13 = 13.0 / 3.0;
-  const double B0 = fma(c13 * s0, s0, t0 * t0);
-  const double B1 = fma(c13 * s1, s1, t1 * t1);
-  const double B2 = fma(c13 * s2, s2, t2 * t2);
-  const double Bd = fma(c13 * s3, s3, t3 * t3);
-  const double B3 = 0.25 * ((B0 + B1) + (B2 + Bd));
   const double r5 = fma(3.0, s1 - s2, s3 - s0);
-  double T = 4.0 * (r5 * r5);
   double e;
   if (AI) {
     // deviations from v2, then from their mean, in FP32
@@ -138,43 +143,60 @@ __device__ __forceinline__ double za6(double v0, double v1, double v2, double v3
     const float m = ((a0 + a1) + (a3 + a4) + a5) * (1.0f / 6.0f);
     const float dev = fabsf(a0 - m) + fabsf(a1 - m) + fabsf(m) + fabsf(a3 - m) + fabsf(a4 - m) +
                       fabsf(a5 - m);
-    const double mu = fma((double)dev, 1.0 / 6.0, P.mu0s);
-    e = P.eps4 * (mu * mu);
+    const double sm = fma((double)dev, P.me, P.mo);  // sqrt(4 eps) mu
+    e = sm * sm;
   } else {
     e = P.efix;
   }
-  const double r0 = fma(5.0, d1, -2.0 * d0);
+  const double c13 = 13.0 / 3.0;
+  double b0 = fma(c13 * s0, s0, fma(t0, t0, e));
+  double b1 = fma(c13 * s1, s1, fma(t1, t1, e));
+  double b2 = fma(c13 * s2, s2, fma(t2, t2, e));
+  const double bd = fma(c13 * s3, s3, fma(t3, t3, e));
+  double b3 = 0.25 * ((b0 + b1) + (b2 + bd));
+  const double r0 = fma(2.0, t0, -d1);
   const double r1 = fma(2.0, d2, d1);
   const double r2 = fma(4.0, d2, -d3);
-  const double r3 = fma(6.0, d2, fma(-5.0, d3, 2.0 * d4));
-  double b0 = B0 + e, b1 = B1 + e, b2 = B2 + e, b3 = B3 + e;
+  const double r3 = fma(6.0, d2, t3 - d4);
+  const double T0 = r5 * r5;  // tau
+  double a0, a1, a2, a3;
   if (P1) {
+    // largest exponent among b_k and 4 tau (bit patterns of positives order
+    // as the numbers; 4 tau by adding 2 to the exponent field)
     unsigned long long mb = max(max(__double_as_longlong(b0), __double_as_longlong(b1)),
                                 max(__double_as_longlong(b2), __double_as_longlong(b3)));
-    mb = max(mb, (unsigned long long)__double_as_longlong(T));
+    mb = max(mb, (unsigned long long)(__double_as_longlong(T0) + (2LL << 52)));
     const long long ex = (long long)((mb >> 52) & 0x7FF);
     const double sc = __longlong_as_double((2046LL - ex) << 52);
     b0 *= sc;
     b1 *= sc;
     b2 *= sc;
     b3 *= sc;
-    T *= sc;
+    const double T = T0 * __longlong_as_double((2048LL - ex) << 52);  // 4 tau sc
     const double p01 = b0 * b1, p23 = b2 * b3;
-    const double a0 = (b0 + T) * (b1 * p23);
-    const double a1 = (b1 + T) * (9.0 * (b0 * p23));
-    const double a2 = (b2 + T) * (9.0 * (b3 * p01));
-    const double a3 = (b3 + T) * (b2 * p01);
-    const double num = fma(a0, r0, fma(a1, r1, fma(a2, r2, a3 * r3)));
-    const double den = 6.0 * ((a0 + a1) + (a2 + a3));
-    return v2 + num / den;
+    a0 = (b0 + T) * (b1 * p23);
+    a1 = (b1 + T) * (b0 * p23);
+    a2 = (b2 + T) * (b3 * p01);
+    a3 = (b3 + T) * (b2 * p01);
   } else {
-    const double g0 = pow(T / b0, P.p), g1 = pow(T / b1, P.p), g2 = pow(T / b2, P.p),
-                 g3 = pow(T / b3, P.p);
-    const double a0 = 1.0 + g0, a1 = 9.0 * (1.0 + g1), a2 = 9.0 * (1.0 + g2), a3 = 1.0 + g3;
-    const double num = fma(a0, r0, fma(a1, r1, fma(a2, r2, a3 * r3)));
-    const double den = 6.0 * ((a0 + a1) + (a2 + a3));
-    return v2 + num / den;
+    const double T = 4.0 * T0;
+    a0 = 1.0 + pow(T / b0, P.p);
+    a1 = 1.0 + pow(T / b1, P.p);
+    a2 = 1.0 + pow(T / b2, P.p);
+    a3 = 1.0 + pow(T / b3, P.p);
   }
+  ZA6Part o;  // the linear weights 1 : 9 : 9 : 1 applied here
+  o.v2 = v2;
+  o.num = fma(9.0, fma(a1, r1, a2 * r2), fma(a0, r0, a3 * r3));
+  o.den = fma(9.0, a1 + a2, a0 + a3);
+  return o;
+}
+
+// f^+_{i+1/2} + f^-_{i+1/2} of one field from its two reconstructions, with
+// one division: v2+ + v2- + (n+ d- + n- d+) / (6 d+ d-).
+__device__ __forceinline__ double pair_flux(const ZA6Part &p, const ZA6Part &m) {
+  const double q = fma(p.num, m.den, m.num * p.den) / (p.den * m.den);
+  return fma(q, 1.0 / 6.0, p.v2 + m.v2);
 }
 
 // ---------------------------------------------------------------------------

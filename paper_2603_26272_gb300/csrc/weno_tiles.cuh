@@ -136,6 +136,9 @@ __device__ __forceinline__ ReconParams make_rp(const StageArgs &a, double k) {
   r.mu0s = k * a.mu0;
   r.efix = 4.0 * a.eps * k * k;
   r.p = a.p;
+  const double se = sqrt(4.0 * a.eps);
+  r.me = se * (1.0 / 6.0);
+  r.mo = se * (k * a.mu0);
   return r;
 }
 
@@ -305,14 +308,14 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
         m4[N - 1 - j] = fma(-A4, w4, g4);
       }
       if constexpr (R == 3) {
-        h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
-             za6<AI, P1>(m1[0], m1[1], m1[2], m1[3], m1[4], m1[5], rp4);
-        h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
-             za6<AI, P1>(m2[0], m2[1], m2[2], m2[3], m2[4], m2[5], rp2);
-        h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp2) +
-             za6<AI, P1>(m3[0], m3[1], m3[2], m3[3], m3[4], m3[5], rp2);
-        h4 = za6<AI, P1>(p4[0], p4[1], p4[2], p4[3], p4[4], p4[5], rp4) +
-             za6<AI, P1>(m4[0], m4[1], m4[2], m4[3], m4[4], m4[5], rp4);
+        h1 = pair_flux(za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4),
+                       za6<AI, P1>(m1[0], m1[1], m1[2], m1[3], m1[4], m1[5], rp4));
+        h2 = pair_flux(za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2),
+                       za6<AI, P1>(m2[0], m2[1], m2[2], m2[3], m2[4], m2[5], rp2));
+        h3 = pair_flux(za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp2),
+                       za6<AI, P1>(m3[0], m3[1], m3[2], m3[3], m3[4], m3[5], rp2));
+        h4 = pair_flux(za6<AI, P1>(p4[0], p4[1], p4[2], p4[3], p4[4], p4[5], rp4),
+                       za6<AI, P1>(m4[0], m4[1], m4[2], m4[3], m4[4], m4[5], rp4));
       } else {
         h1 = za_r<R, AI, P1>(p1, rp4) + za_r<R, AI, P1>(m1, rp4);
         h2 = za_r<R, AI, P1>(p2, rp2) + za_r<R, AI, P1>(m2, rp2);
@@ -466,8 +469,8 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             mm[N - 1 - j] = fma(-A, v, fv);
           }
           if constexpr (R == 3)
-            h = za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp) +
-                za6<AI, P1>(mm[0], mm[1], mm[2], mm[3], mm[4], mm[5], rp);
+            h = pair_flux(za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp),
+                          za6<AI, P1>(mm[0], mm[1], mm[2], mm[3], mm[4], mm[5], rp));
           else
             h = za_r<R, AI, P1>(pp, rp) + za_r<R, AI, P1>(mm, rp);
         }
@@ -511,12 +514,12 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             m3[N - 1 - j] = fma(-A3, w3, g3);
           }
           if constexpr (R == 3) {
-            h1 = za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4) +
-                 za6<AI, P1>(m1[0], m1[1], m1[2], m1[3], m1[4], m1[5], rp4);
-            h2 = za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2) +
-                 za6<AI, P1>(m2[0], m2[1], m2[2], m2[3], m2[4], m2[5], rp2);
-            h3 = za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp4) +
-                 za6<AI, P1>(m3[0], m3[1], m3[2], m3[3], m3[4], m3[5], rp4);
+            h1 = pair_flux(za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4),
+                           za6<AI, P1>(m1[0], m1[1], m1[2], m1[3], m1[4], m1[5], rp4));
+            h2 = pair_flux(za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2),
+                           za6<AI, P1>(m2[0], m2[1], m2[2], m2[3], m2[4], m2[5], rp2));
+            h3 = pair_flux(za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp4),
+                           za6<AI, P1>(m3[0], m3[1], m3[2], m3[3], m3[4], m3[5], rp4));
           } else {
             h1 = za_r<R, AI, P1>(p1, rp4) + za_r<R, AI, P1>(m1, rp4);
             h2 = za_r<R, AI, P1>(p2, rp2) + za_r<R, AI, P1>(m2, rp2);
@@ -599,8 +602,11 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
     // tile variants (cells / threads / blocks per SM the registers allow):
     // 0 = 32x16 / 256 / 1 (fewest halo faces), 1 = 16x16 / 128 / 2,
     // 2 = 16x8 / 64 / 4 (more tiles for small grids), 3 = 16x16 / 128 / 3,
-    // 4 = 16x8 / 64 / 6.  The other orders use 16x16 / 128 / 2 only (their
-    // wider halo and stencil).
+    // 4 = 16x8 / 64 / 6, and two shapes whose face count is a multiple of
+    // the block's threads, so every warp computes the same number of faces:
+    // 5 = 20x12 / 128 / 3 (512 faces), 6 = 26x14 / 128 / 3 (768 faces).
+    // The other orders use 16x16 / 128 / 2 only (their wider halo and
+    // stencil).
     if constexpr (R != 3) {
       return launch_2d<16, 16, 128, 2, AI, P1, PREC, R>(a, s);
     } else {
@@ -609,6 +615,8 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
         case 2: return launch_2d<16, 8, 64, 4, AI, P1, PREC>(a, s);
         case 3: return launch_2d<16, 16, 128, 3, AI, P1, PREC>(a, s);
         case 4: return launch_2d<16, 8, 64, 6, AI, P1, PREC>(a, s);
+        case 5: return launch_2d<20, 12, 128, 3, AI, P1, PREC>(a, s);
+        case 6: return launch_2d<26, 14, 128, 3, AI, P1, PREC>(a, s);
         default: return launch_2d<kTX, kTY, kThreads2D, 1, AI, P1, PREC>(a, s);
       }
     }

@@ -115,3 +115,53 @@ def test_division_free_weights():
             (bs[3] + Ts) * (bs[2] * (bs[0] * bs[1]))]
     for k in range(4):
         assert sp.simplify(paper[k] / sum(paper) - kern[k] / sum(kern)) == 0
+
+
+def test_candidate_corrections_share_the_indicator_terms():
+    # r0 = 5d1 - 2d0 = 2 t0 - d1 and r3 = 6d2 - 5d3 + 2d4 = 6d2 + (t3 - d4)
+    t0 = 3 * d[1] - d[0]
+    t3 = 3 * d[4] - 5 * d[3]
+    assert sp.expand((2 * t0 - d[1]) - (5 * d[1] - 2 * d[0])) == 0
+    assert sp.expand((6 * d[2] + (t3 - d[4])) - (6 * d[2] - 5 * d[3] + 2 * d[4])) == 0
+
+
+def test_partial_sums_and_pair_flux():
+    # za6 returns v2, num = sum a_k r_k (with d_1/d_0 = 9 applied as
+    # 9 (a1 r1 + a2 r2)), den = a0 + a3 + 9 (a1 + a2); the flux is
+    # v2 + num / (6 den); pair_flux adds two of them with one division.
+    a = sp.symbols("a0:4", positive=True)
+    r = sp.symbols("r0:4")
+    v2p, v2m = sp.symbols("v2p v2m")
+    num = 9 * (a[1] * r[1] + a[2] * r[2]) + (a[0] * r[0] + a[3] * r[3])
+    den = 9 * (a[1] + a[2]) + (a[0] + a[3])
+    w = [a[0], 9 * a[1], 9 * a[2], a[3]]
+    want = v2p + sum(w[k] * r[k] / 6 for k in range(4)) / sum(w)
+    assert sp.simplify(v2p + num / (6 * den) - want) == 0
+    np_, dp, nm, dm = sp.symbols("n_p d_p n_m d_m", positive=True)
+    pair = (v2p + v2m) + (np_ * dm + nm * dp) / (dp * dm) / 6
+    assert sp.simplify(pair - (v2p + np_ / (6 * dp) + v2m + nm / (6 * dm))) == 0
+
+
+def test_flux_projection_from_state_projection():
+    # F = u_n U + p (0, 1, 0, u_n) in the normal frame (eq. (25)), so the
+    # characteristic values of F follow from those of U, u_n and p.
+    un, ut, c, g = sp.symbols("u_n u_t c gamma", positive=True)
+    q2 = un ** 2 + ut ** 2
+    b1 = (g - 1) / c ** 2
+    b2 = b1 * q2 / 2
+
+    def project4(rho, mn, mt, E):
+        sx = un * mn + ut * mt - E
+        z = b2 * rho - b1 * sx
+        tc = (un * rho - mn) / c
+        return sp.Matrix([z + tc, rho - z, mt - ut * rho, z - tc])
+
+    rho, uj, vt, p = sp.symbols("rho u_j v_t p", positive=True)
+    mn, mt = rho * uj, rho * vt
+    E = p / (g - 1) + rho * (uj ** 2 + vt ** 2) / 2
+    F = [mn, mn * uj + p, mt * uj, (E + p) * uj]
+    w = project4(rho, mn, mt, E)
+    z = b1 * (uj - un)
+    kern = sp.Matrix([uj * w[0] + (p * z - p / c), uj * w[1] - p * z, uj * w[2],
+                      uj * w[3] + (p * z + p / c)])
+    assert sp.simplify(kern - project4(*F)) == sp.zeros(4, 1)
