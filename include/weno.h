@@ -73,8 +73,8 @@ typedef struct weno_desc {
   int32_t bc_x, bc_y; /* WENO_BC_*: r ghost cells per side, zero-gradient or wrap */
   double gamma;       /* ratio of specific heats (Euler)                          */
   double cfl;         /* CFL number of the time step rule                         */
-  double eps;         /* sensitivity epsilon of eq. (21)                          */
-  double mu0;         /* mu_0 of eq. (22)                                         */
+  double eps;         /* sensitivity epsilon of eq. (21); with ai = 1, >= 1e-250  */
+  double mu0;         /* mu_0 of eq. (22); with ai = 1, >= 1e-100                 */
   double p;           /* power parameter p of eq. (21), >= 1                      */
   int32_t ai;         /* 1: affine-invariant descaler mu[f] of eq. (22); 0: mu = 1 */
   int32_t precision;  /* WENO_PREC_FP64 (FP32_RECON is reserved)                  */

@@ -107,6 +107,8 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 // adds the positive and negative fluxes of a field with one division.
 // b_k = 4 beta_k + 4 eps mu^2 is formed as 13/3 s_k^2 + (t_k^2 + e), and
 // b_3 = mean of b_0, b_1, b_2, b_d (the same number as 4 beta_3 + e).
+// (The bound on the spread of the b_k with Ai: each 4 beta_k is at most ~1e4
+// mu^2 and e = 4e-40 mu^2, so min b / max b > ~1e-44.)
 //
 // For p = 1 the four divisions tau/b_k are removed: a_k = (b_k + 4 tau)
 // prod_{j != k} b_j (times d_k / d_0).  Before the products, the b_k and
@@ -153,7 +155,7 @@ __device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v
   double b1 = fma(c13 * s1, s1, fma(t1, t1, e));
   double b2 = fma(c13 * s2, s2, fma(t2, t2, e));
   const double bd = fma(c13 * s3, s3, fma(t3, t3, e));
-  double b3 = 0.25 * ((b0 + b1) + (b2 + bd));
+  const double bsum = (b0 + b1) + (b2 + bd);  // 4 b_3
   const double r0 = fma(2.0, t0, -d1);
   const double r1 = fma(2.0, d2, d1);
   const double r2 = fma(4.0, d2, -d3);
@@ -162,17 +164,31 @@ __device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v
   double a0, a1, a2, a3;
   if (P1) {
     // largest exponent among b_k and 4 tau (bit patterns of positives order
-    // as the numbers; 4 tau by adding 2 to the exponent field)
+    // as the numbers; 4 tau by adding 2 to the exponent field; b_3 is a mean
+    // of the others and never the largest)
     unsigned long long mb = max(max(__double_as_longlong(b0), __double_as_longlong(b1)),
-                                max(__double_as_longlong(b2), __double_as_longlong(b3)));
+                                max(__double_as_longlong(b2), __double_as_longlong(bd)));
     mb = max(mb, (unsigned long long)(__double_as_longlong(T0) + (2LL << 52)));
-    const long long ex = (long long)((mb >> 52) & 0x7FF);
-    const double sc = __longlong_as_double((2046LL - ex) << 52);
-    b0 *= sc;
-    b1 *= sc;
-    b2 *= sc;
-    b3 *= sc;
-    const double T = T0 * __longlong_as_double((2048LL - ex) << 52);  // 4 tau sc
+    const int ex = (int)((mb >> 52) & 0x7FF);
+    double b3;
+    if (AI) {
+      // With the affine-invariant e every b_k is within a factor ~1e-44 of
+      // the largest, so the scaled values stay normal and the scaling by
+      // 2^(1023 - ex) is an exact add to the exponent field (integer pipe);
+      // b_3 = bsum / 4 takes exponent - 2 in the same add.
+      const int k = (1023 - ex) << 20;
+      b0 = __hiloint2double(__double2hiint(b0) + k, __double2loint(b0));
+      b1 = __hiloint2double(__double2hiint(b1) + k, __double2loint(b1));
+      b2 = __hiloint2double(__double2hiint(b2) + k, __double2loint(b2));
+      b3 = __hiloint2double(__double2hiint(bsum) + k - (2 << 20), __double2loint(bsum));
+    } else {
+      const double sc = __longlong_as_double((2046LL - ex) << 52);
+      b0 *= sc;
+      b1 *= sc;
+      b2 *= sc;
+      b3 = bsum * (0.25 * sc);
+    }
+    const double T = T0 * __longlong_as_double((2048LL - ex) << 52);  // 4 tau, scaled
     const double p01 = b0 * b1, p23 = b2 * b3;
     a0 = (b0 + T) * (b1 * p23);
     a1 = (b1 + T) * (b0 * p23);
@@ -180,6 +196,7 @@ __device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v
     a3 = (b3 + T) * (b2 * p01);
   } else {
     const double T = 4.0 * T0;
+    const double b3 = 0.25 * bsum;
     a0 = 1.0 + pow(T / b0, P.p);
     a1 = 1.0 + pow(T / b1, P.p);
     a2 = 1.0 + pow(T / b2, P.p);

@@ -51,6 +51,7 @@ def test_workspace_bytes_and_argument_checks(L):
     bad = [dict(ndim=3), dict(nx=0), dict(ndim=1, ny=2), dict(gamma=1.0), dict(cfl=0.0),
            dict(eps=0.0), dict(precision="fp32_recon", ai=False), dict(system="advection", ndim=2, ny=4),
            dict(nbatch=70000), dict(x1=0.0), dict(order=5), dict(order=12), dict(order=2),
+           dict(eps=1e-260), dict(mu0=1e-120),
            dict(order=8, precision="fp32_recon")]
     for kw in bad:
         args = dict(system="euler", ndim=2, nx=8, ny=8)
