@@ -199,12 +199,12 @@ def scheme_orders(weno, wl, torch, n=N_GRID, steps=4, warmup=3):
 WORK_BUDGET = 250e3
 
 
-def serving(n_requests=100, seed=5):
+def serving(n_requests=100, seed=5, loads=(1.0, 1.25)):
     """Configuration 5, scaled to about a minute: a seeded stream of mixed
     1D/2D, FP64/FP32-reconstruction solves.  The offered Poisson rate is set
-    to 1.0x the one-at-a-time capacity (measured first on the same GPU); the
-    same arrivals are then served one at a time (weno_solve, FIFO) and by the
-    continuous-batching engine."""
+    to `loads` x the one-at-a-time capacity (measured first on the same GPU);
+    at each load the same arrivals are served one at a time (weno_solve, FIFO)
+    and by the continuous-batching engine."""
     import torch
     from paper_2603_26272_gb300 import serve
     sides, n1d, steps = (128, 192, 256), (256, 16384), (100, 300)
@@ -213,19 +213,32 @@ def serving(n_requests=100, seed=5):
     serve.serve_one_at_a_time(reqs)  # calibration: service times back to back
     service = [r.result["done"] - r.result["admit"] for r in reqs]
     calib_thr = serve.summarize(reqs)["throughput_cell_updates_per_s"]
-    rate = 1.0 / float(np.mean(service))
-    gaps = np.random.default_rng(seed + 1).exponential(1.0 / rate, size=len(reqs))
-    arr = np.cumsum(gaps) - gaps[0]
-    for r, a in zip(reqs, arr):
-        r.arrival = float(a)
-        r.result = {}
-    base = serve.summarize(serve.serve_one_at_a_time(reqs))
-    for r in reqs:
-        r.result = {}
     free = torch.cuda.mem_get_info()[0]
     eng = serve.Engine(arena_bytes=int(min(8 << 30, free // 2)), max_slots=256)
-    cont = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2,
-                                                  work_budget=WORK_BUDGET))
+    out = {"workload": "%d requests: 50%% 1D Euler Riemann (N log-uniform %d..%d), 50%% 2D "
+                       "quadrant (side in %s); 50%% FP64, 50%% FP32-recon; %d..%d steps each; "
+                       "Poisson arrivals (seed %d)" % (n_requests, n1d[0], n1d[1], list(sides),
+                                                       steps[0], steps[1], seed),
+           "work_budget_cell_units": WORK_BUDGET, "loads": []}
+    for load in loads:
+        rate = load / float(np.mean(service))
+        gaps = np.random.default_rng(seed + 1).exponential(1.0 / rate, size=len(reqs))
+        arr = np.cumsum(gaps) - gaps[0]
+        for r, a in zip(reqs, arr):
+            r.arrival = float(a)
+            r.result = {}
+        base = serve.summarize(serve.serve_one_at_a_time(reqs))
+        for r in reqs:
+            r.result = {}
+        cont = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2,
+                                                      work_budget=WORK_BUDGET))
+        out["loads"].append({
+            "offered_load_vs_one_at_a_time": load, "offered_rate_per_s": rate,
+            "one_at_a_time": base, "continuous_batching": cont,
+            "throughput_ratio": (cont["throughput_cell_updates_per_s"]
+                                 / base["throughput_cell_updates_per_s"]),
+            "p50_ratio": cont["p50_latency_s"] / base["p50_latency_s"],
+            "p99_ratio": cont["p99_latency_s"] / base["p99_latency_s"]})
     # capacity: every request present at t = 0, engine versus the back-to-back
     # one-at-a-time calibration run above
     for r in reqs:
@@ -234,19 +247,10 @@ def serving(n_requests=100, seed=5):
     sat = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2,
                                                  work_budget=WORK_BUDGET))
     eng.close()
-    return {"workload": "%d requests: 50%% 1D Euler Riemann (N log-uniform %d..%d), 50%% 2D "
-                        "quadrant (side in %s); 50%% FP64, 50%% FP32-recon; %d..%d steps each; "
-                        "Poisson arrivals (seed %d)" % (n_requests, n1d[0], n1d[1], list(sides),
-                                                        steps[0], steps[1], seed),
-            "offered_rate_per_s": rate, "offered_load_vs_one_at_a_time": 1.0,
-            "one_at_a_time": base, "continuous_batching": cont,
-            "throughput_ratio": cont["throughput_cell_updates_per_s"] / base["throughput_cell_updates_per_s"],
-            "p50_ratio": cont["p50_latency_s"] / base["p50_latency_s"],
-            "p99_ratio": cont["p99_latency_s"] / base["p99_latency_s"],
-            "work_budget_cell_units": WORK_BUDGET,
-            "capacity_one_at_a_time_cell_updates_per_s": calib_thr,
-            "capacity_continuous_cell_updates_per_s": sat["throughput_cell_updates_per_s"],
-            "capacity_ratio": sat["throughput_cell_updates_per_s"] / calib_thr}
+    out.update({"capacity_one_at_a_time_cell_updates_per_s": calib_thr,
+                "capacity_continuous_cell_updates_per_s": sat["throughput_cell_updates_per_s"],
+                "capacity_ratio": sat["throughput_cell_updates_per_s"] / calib_thr})
+    return out
 
 
 def cpu_baseline(seconds, window=256):

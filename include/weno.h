@@ -179,8 +179,12 @@ weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, double *dUdt, 
  * step to its own t_final; all admitted slots advance together, every engine
  * step being one SSP-RK3 step of each unfinished slot (three launches of a
  * persistent kernel over a device work list of all slots' tiles, replayed as
- * one CUDA graph).  Problems can be admitted and retired between runs.  The
- * paper has no serving layer: this is how many of its solves share a GPU.
+ * one CUDA graph).  A slot marked fast (weno_engine_set_fast) advances
+ * WENO_ENGINE_FAST_STEPS SSP-RK3 steps per engine step: the graph then holds
+ * that many sub-steps, the first over every slot, the others over the fast
+ * slots only, so small or urgent solves need not wait for the pace of the
+ * largest.  Problems can be admitted and retired between runs.  The paper
+ * has no serving layer: this is how many of its solves share a GPU.
  *
  * Memory: `arena` is caller-owned DEVICE memory (256-byte aligned).  Its first
  * weno_engine_control_bytes(max_slots, max_tiles) bytes hold the engine's
@@ -204,6 +208,12 @@ weno_status weno_engine_admit(weno_engine *e, const weno_desc *d, const double *
                               double t_final, int *slot_out);
 /* Enqueue nsteps engine steps (asynchronous). */
 weno_status weno_engine_run(weno_engine *e, int nsteps);
+/* SSP-RK3 steps per engine step of a fast slot. */
+#define WENO_ENGINE_FAST_STEPS 4
+/* Mark an admitted slot fast (fast = 1: WENO_ENGINE_FAST_STEPS steps per
+ * engine step) or normal (0: one step).  Takes effect at the next run(); a
+ * slot's results are the same bit for bit either way. */
+weno_status weno_engine_set_fast(weno_engine *e, int slot, int fast);
 /* Wait for the enqueued steps; done[0..min(*n_done, max_done)) receives the
  * slots that reached t_final or met a nonphysical state; n_active (may be
  * NULL) the number of admitted slots. */

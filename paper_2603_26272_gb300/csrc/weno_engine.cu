@@ -12,7 +12,10 @@
 //    arguments never change -- admission and retirement only rewrite the work
 //    list and the slot table in device memory;
 //  * each slot advances with its own CFL step to its own t_final; finished
-//    slots stop (their tiles return at once) until the host retires them.
+//    slots stop (their tiles return at once) until the host retires them;
+//  * a fast slot takes WENO_ENGINE_FAST_STEPS steps per engine step: its
+//    tiles sit at the end of the work list, and the graph used while any
+//    slot is fast repeats the three launches over that tail.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -41,7 +44,7 @@ weno_status ecuda(cudaError_t e, const char *what) {
 }
 
 struct ControlLayout {
-  size_t slots, tiles, ntiles, counters, alpha, clock, steps, status, total;
+  size_t slots, tiles, ntiles, first, counters, alpha, clock, steps, status, total;
 };
 
 ControlLayout control_layout(int max_slots, long long max_tiles) {
@@ -53,6 +56,8 @@ ControlLayout control_layout(int max_slots, long long max_tiles) {
   o = align256(o + sizeof(EngineTile) * (size_t)max_tiles);
   L.ntiles = o;
   o = align256(o + sizeof(int));
+  L.first = o;  // [0] = 0, [1] = first entry of the fast slots' tiles
+  o = align256(o + 2 * sizeof(int));
   L.counters = o;
   o = align256(o + 3 * sizeof(int));
   L.alpha = o;
@@ -69,6 +74,7 @@ ControlLayout control_layout(int max_slots, long long max_tiles) {
 
 struct SlotHost {
   bool used = false;
+  bool fast = false;
   int ndim = 0, precision = 0;
   long long cells = 0, tiles = 0;
   size_t off = 0, bytes = 0, state_bytes = 0;
@@ -89,12 +95,15 @@ struct weno_engine {
   std::vector<SlotDev> mirror;
   bool dirty = true;
   long long tiles_in_use = 0;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;       // one sub-step per engine step
+  cudaGraphExec_t graph_fast = nullptr;  // WENO_ENGINE_FAST_STEPS sub-steps
+  int n_fast = 0;                        // used slots marked fast
   int grid = 0;
 
   SlotDev *d_slots() const { return (SlotDev *)(arena + L.slots); }
   EngineTile *d_tiles() const { return (EngineTile *)(arena + L.tiles); }
   int *d_ntiles() const { return (int *)(arena + L.ntiles); }
+  int *d_first() const { return (int *)(arena + L.first); }
   int *d_counters() const { return (int *)(arena + L.counters); }
   unsigned long long *d_alpha(int k) const { return (unsigned long long *)(arena + L.alpha) + 24 * k; }
   double *d_clock(int k) const { return (double *)(arena + L.clock) + 3 * k; }
@@ -138,26 +147,33 @@ struct weno_engine {
 
 namespace {
 
-// Upload the slot table and the work list: tiles of the costliest classes
-// first (2D FP64, 2D FP32, 1D), so the atomic work counter hands out the
-// long tiles early and the short ones fill the tail.
+// Upload the slot table and the work list: the normal slots' tiles, then the
+// fast slots' tiles; within each part the costliest classes first (2D FP64,
+// 2D FP32, 1D), so the atomic work counter hands out the long tiles early
+// and the short ones fill the tail.
 weno_status upload(weno_engine *E) {
   std::vector<EngineTile> list;
   list.reserve((size_t)E->tiles_in_use);
   const int order[3][2] = {{2, 0}, {2, 1}, {1, -1}};
-  for (auto &cls : order)
-    for (int k = 0; k < E->max_slots; ++k) {
-      const SlotHost &h = E->slots[k];
-      if (!h.used || h.ndim != cls[0]) continue;
-      if (cls[1] >= 0 && h.precision != cls[1]) continue;
-      for (long long t = 0; t < h.tiles; ++t) list.push_back({k, (int)t});
-    }
+  int first[2] = {0, 0};
+  for (int part = 0; part < 2; ++part) {
+    if (part == 1) first[1] = (int)list.size();
+    for (auto &cls : order)
+      for (int k = 0; k < E->max_slots; ++k) {
+        const SlotHost &h = E->slots[k];
+        if (!h.used || h.fast != (part == 1) || h.ndim != cls[0]) continue;
+        if (cls[1] >= 0 && h.precision != cls[1]) continue;
+        for (long long t = 0; t < h.tiles; ++t) list.push_back({k, (int)t});
+      }
+  }
   const int n = (int)list.size();
   cudaError_t e = cudaSuccess;
   if (n) e = cudaMemcpyAsync(E->d_tiles(), list.data(), sizeof(EngineTile) * n,
                              cudaMemcpyHostToDevice, E->s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(E->d_ntiles(), &n, sizeof(int), cudaMemcpyHostToDevice, E->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(E->d_first(), first, sizeof(first), cudaMemcpyHostToDevice, E->s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(E->d_slots(), E->mirror.data(), sizeof(SlotDev) * E->max_slots,
                         cudaMemcpyHostToDevice, E->s);
@@ -168,7 +184,10 @@ weno_status upload(weno_engine *E) {
   return WENO_OK;
 }
 
-weno_status build_graph(weno_engine *E) {
+// One engine step as a graph of `substeps` x 3 stage launches: the first
+// sub-step over the whole work list, the others from the fast slots' first
+// entry on.
+weno_status build_graph(weno_engine *E, int substeps, cudaGraphExec_t *out) {
   weno::EngineArgs a;
   a.slots = E->d_slots();
   a.tiles = E->d_tiles();
@@ -177,15 +196,18 @@ weno_status build_graph(weno_engine *E) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(E->s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return ecuda(e, "cudaStreamBeginCapture");
-  for (int st = 1; st <= 3; ++st) {
-    a.stage = st;
-    e = weno::launch_engine_stage(a, E->grid, E->s);
-    if (e != cudaSuccess) break;
+  for (int sub = 0; sub < substeps && e == cudaSuccess; ++sub) {
+    a.first = E->d_first() + (sub == 0 ? 0 : 1);
+    for (int st = 1; st <= 3; ++st) {
+      a.stage = st;
+      e = weno::launch_engine_stage(a, E->grid, E->s);
+      if (e != cudaSuccess) break;
+    }
   }
   cudaError_t e2 = cudaStreamEndCapture(E->s, &g);
   if (e != cudaSuccess) return ecuda(e, "engine stage capture");
   if (e2 != cudaSuccess) return ecuda(e2, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&E->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return ecuda(e, "cudaGraphInstantiate");
   return WENO_OK;
@@ -250,9 +272,11 @@ weno_status weno_engine_create(void *arena, size_t arena_bytes, int max_slots, i
     return ecuda(e, "engine control reset");
   }
   weno_status st = upload(E);
-  if (st == WENO_OK) st = build_graph(E);
+  if (st == WENO_OK) st = build_graph(E, 1, &E->graph);
+  if (st == WENO_OK) st = build_graph(E, WENO_ENGINE_FAST_STEPS, &E->graph_fast);
   if (st != WENO_OK) {
     if (E->graph) cudaGraphExecDestroy(E->graph);
+    if (E->graph_fast) cudaGraphExecDestroy(E->graph_fast);
     if (E->own_stream) cudaStreamDestroy(E->s);
     delete E;
     return st;
@@ -364,9 +388,23 @@ weno_status weno_engine_run(weno_engine *E, int nsteps) {
     weno_status st = upload(E);
     if (st != WENO_OK) return st;
   }
+  cudaGraphExec_t g = E->n_fast > 0 ? E->graph_fast : E->graph;
   for (int q = 0; q < nsteps; ++q) {
-    cudaError_t e = cudaGraphLaunch(E->graph, E->s);
+    cudaError_t e = cudaGraphLaunch(g, E->s);
     if (e != cudaSuccess) return ecuda(e, "cudaGraphLaunch");
+  }
+  return WENO_OK;
+}
+
+weno_status weno_engine_set_fast(weno_engine *E, int slot, int fast) {
+  if (!E || slot < 0 || slot >= E->max_slots || !E->slots[slot].used)
+    return efail(WENO_ERR_ARG, "no such slot");
+  if (fast != 0 && fast != 1) return efail(WENO_ERR_ARG, "fast must be 0 or 1");
+  SlotHost &h = E->slots[slot];
+  if (h.fast != (fast == 1)) {
+    h.fast = fast == 1;
+    E->n_fast += fast ? 1 : -1;
+    E->dirty = true;
   }
   return WENO_OK;
 }
@@ -417,6 +455,7 @@ weno_status weno_engine_retire(weno_engine *E, int slot, double *U_host, double 
   if (steps_out) *steps_out = steps;
   E->heap_free(h.off, h.bytes);
   E->tiles_in_use -= h.tiles;
+  if (h.fast) --E->n_fast;
   h = SlotHost();
   std::memset(&S, 0, sizeof(S));
   E->dirty = true;
@@ -444,6 +483,7 @@ weno_status weno_engine_destroy(weno_engine *E) {
   if (!E) return WENO_OK;
   cudaStreamSynchronize(E->s);
   if (E->graph) cudaGraphExecDestroy(E->graph);
+  if (E->graph_fast) cudaGraphExecDestroy(E->graph_fast);
   if (E->own_stream) cudaStreamDestroy(E->s);
   delete E;
   return WENO_OK;

@@ -84,12 +84,14 @@ struct EngineArgs {
   const SlotDev *slots;
   const EngineTile *tiles;
   const int *ntiles;
+  const int *first;             // first work-list entry of this launch (0, or
+                                // the start of the fast slots' tiles)
   int *counters;                // [3] rotating work counters
   int stage;                    // 1, 2, 3
 };
 
 constexpr int kEngineThreads = 128;
-constexpr int kEngineBlocksPerSM = 2;
+constexpr int kEngineBlocksPerSM = 3;
 constexpr int kEngine1DCells = kEngineThreads - 1;
 constexpr int kEngineTX = 16, kEngineTY = 16;
 size_t engine_smem_bytes();

@@ -93,9 +93,11 @@ __global__ void k_fill(double *p, long long n, double v) {
 
 
 // ---------------------------------------------------------------------------
-// Serving engine stage kernel.  A persistent grid (one 256-thread block per
-// SM) takes tiles from the device-resident work list with an atomic counter
-// (heaviest tiles first in the list) and runs the same tile functions as the
+// Serving engine stage kernel.  A persistent grid (kEngineBlocksPerSM blocks
+// of kEngineThreads per SM) takes tiles from the device-resident work list,
+// from entry *first on, with an atomic counter (heaviest tiles first in the
+// list; the fast slots' tiles last, so a sub-step over the fast slots only
+// starts at their first entry) and runs the same tile functions as the
 // single-problem kernels, on the slot's own buffers, speed slots and clock.
 // The counter of the launch after next is cleared here, so consecutive
 // launches never wait on the host.  Restricted to the scheme's default
@@ -150,9 +152,9 @@ __global__ void __launch_bounds__(kEngineThreads, kEngineBlocksPerSM) k_engine(c
   __shared__ int s_w;
   const int cin = e.stage - 1, czero = (e.stage + 1) % 3;
   if (blockIdx.x == 0 && threadIdx.x == 0) e.counters[czero] = 0;
-  const int ntiles = *e.ntiles;
+  const int ntiles = *e.ntiles, first = *e.first;
   for (;;) {
-    if (threadIdx.x == 0) s_w = atomicAdd(&e.counters[cin], 1);
+    if (threadIdx.x == 0) s_w = first + atomicAdd(&e.counters[cin], 1);
     __syncthreads();
     const int w = s_w;
     __syncthreads();

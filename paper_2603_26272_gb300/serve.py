@@ -41,6 +41,8 @@ class _EngineLib:
                                         ctypes.c_double, P(ctypes.c_int)]
         L.weno_engine_run.restype = ctypes.c_int
         L.weno_engine_run.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.weno_engine_set_fast.restype = ctypes.c_int
+        L.weno_engine_set_fast.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.weno_engine_poll.restype = ctypes.c_int
         L.weno_engine_poll.argtypes = [ctypes.c_void_p, P(ctypes.c_int), ctypes.c_int,
                                        P(ctypes.c_int), P(ctypes.c_int)]
@@ -63,6 +65,9 @@ def _lib():
     if _elib is None:
         _elib = _EngineLib()
     return _elib.L
+
+
+FAST_STEPS = 4  # WENO_ENGINE_FAST_STEPS of include/weno.h
 
 
 class Engine:
@@ -102,6 +107,10 @@ class Engine:
 
     def run(self, nsteps):
         weno._check(_lib().weno_engine_run(self.h, int(nsteps)))
+
+    def set_fast(self, slot, fast=True):
+        """Fast slots take FAST_STEPS SSP-RK3 steps per engine step."""
+        weno._check(_lib().weno_engine_set_fast(self.h, int(slot), int(bool(fast))))
 
     def poll(self):
         done = (ctypes.c_int * self.max_slots)()
@@ -200,7 +209,7 @@ def work_units(r):
 
 
 def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, work_budget=None,
-                     clock=time.perf_counter):
+                     fast=None, fast_units=0.0, clock=time.perf_counter):
     """Continuous batching in real time.  Fills request.result with arrival,
     admit and completion times (seconds from the start), steps, status.
 
@@ -209,17 +218,47 @@ def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, work
     request that does not fit lets later, smaller ones pass) and, when
     `work_budget` is set, the admitted solves' cost per step (work_units)
     must stay within it, so the GPU is kept full without stretching every
-    solve by sharing it with all others."""
+    solve by sharing it with all others.
+
+    Every admitted solve advances one SSP-RK3 step per engine step, except
+    the fast ones, which take FAST_STEPS (the engine repeats the launches over
+    their tiles only).  `fast` chooses them: None (no fast slots), "light"
+    (every solve costing at most `fast_units` per step), or "oldest" (the
+    longest-admitted solves, in admission order, while their summed cost
+    stays within `fast_units`) -- the second keeps the order of completion
+    close to first-come first-served while the younger solves fill the GPU."""
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     waiting = []
     active = {}
+    order = []  # admitted slots, oldest first
+    marked = set()
     load = 0.0
     t0 = clock()
+
+    def mark_fast():
+        want = set()
+        if fast == "light":
+            want = {k for k in order if work_units(active[k]) <= fast_units}
+        elif fast == "oldest":
+            acc = 0.0
+            for k in order:
+                acc += work_units(active[k])
+                if acc > fast_units:
+                    break
+                want.add(k)
+        for k in marked - want:
+            engine.set_fast(k, False)
+        for k in want - marked:
+            engine.set_fast(k, True)
+        marked.clear()
+        marked.update(want)
+
     while pending or waiting or active:
         now = clock() - t0
         while pending and pending[0].arrival <= now:
             waiting.append(pending.popleft())
         still = []
+        changed = False
         for i, r in enumerate(waiting):
             wu = work_units(r)
             if work_budget is not None and active and load + wu > work_budget:
@@ -231,18 +270,26 @@ def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, work
                 continue
             r.result["admit"] = clock() - t0
             active[slot] = r
+            order.append(slot)
             load += wu
+            changed = True
         waiting = still
+        if changed and fast:
+            mark_fast()
         if active:
             engine.run(steps_per_poll)
             done, _ = engine.poll()
             for slot in done:
                 U, t, n, code = engine.retire(slot, want_state=keep_states)
                 r = active.pop(slot)
+                order.remove(slot)
+                marked.discard(slot)
                 load -= work_units(r)
                 r.result.update({"done": clock() - t0, "t": t, "steps": n, "status": code})
                 if keep_states:
                     r.result["U"] = U
+            if done and fast:
+                mark_fast()
         elif pending:
             time.sleep(max(0.0, min(pending[0].arrival - (clock() - t0), 0.01)))
     for r in requests:

@@ -44,6 +44,38 @@ def test_alone_equals_in_the_mix():
     eng.close()
 
 
+@pytest.mark.parametrize("fast,units", [("light", 3000.0), ("oldest", 8000.0)])
+def test_fast_slots_equal_alone(fast, units):
+    """Fast slots take several SSP-RK3 steps per engine step (the engine
+    repeats the launches over their tiles); the results stay bitwise those of
+    the solve alone, for the fast and the normal slots."""
+    reqs = serve.make_requests(10, seed=24, sides_2d=(40, 64, 100), n1d=(60, 3000), steps=(15, 60))
+    eng = serve.Engine(arena_bytes=512 << 20, max_slots=32)
+    serve.serve_continuous(eng, reqs, steps_per_poll=2, keep_states=True, fast=fast,
+                           fast_units=units)
+    for r in reqs:
+        U, t, n = _alone(r)
+        assert r.result["status"] == 0
+        assert r.result["steps"] == n and r.result["t"] == t
+        assert np.array_equal(r.result["U"], U), r.rid
+    eng.close()
+
+
+def test_fast_slot_advances_several_steps_per_engine_step():
+    w = wl.riemann_batch(nbatch=1, n=500, seed=3)
+    d = weno.desc_for(w)
+    eng = serve.Engine(arena_bytes=64 << 20, max_slots=4, max_tiles=4096)
+    a = eng.admit(d, w["U"], 1e9)
+    b = eng.admit(d, w["U"], 1e9)
+    eng.set_fast(b)
+    eng.run(3)
+    eng.poll()
+    _, _, na, _ = eng.retire(a, want_state=False)
+    _, _, nb, _ = eng.retire(b, want_state=False)
+    assert na == 3 and nb == 3 * serve.FAST_STEPS
+    eng.close()
+
+
 def test_poisoned_request_fails_alone():
     reqs = serve.make_requests(6, seed=22, sides_2d=(48,), n1d=(100, 400), steps=(20, 40))
     bad = reqs[2]

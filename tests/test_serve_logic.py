@@ -31,6 +31,7 @@ class FakeEngine:
         self.slots = {}
         self.next = 0
         self.admitted = []
+        self.fast_log = []
 
     def admit(self, desc, U, t_final):
         r = desc
@@ -43,14 +44,21 @@ class FakeEngine:
         self.admitted.append(r.rid)
         return s
 
+    fast = ()
+
+    def set_fast(self, slot, fast=True):
+        self.fast = tuple(sorted(set(self.fast) - {slot} | ({slot} if fast else set())))
+        self.fast_log.append((slot, fast))
+
     def run(self, n):
-        for v in self.slots.values():
-            v[1] += n
+        for s, v in self.slots.items():
+            v[1] += n * (serve.FAST_STEPS if s in self.fast else 1)
 
     def poll(self):
         return [s for s, v in self.slots.items() if v[1] >= v[0].steps_needed], len(self.slots)
 
     def retire(self, slot, want_state=True):
+        self.fast = tuple(x for x in self.fast if x != slot)
         r, n = self.slots.pop(slot)
         self.used -= r.size
         return None, 1.0, r.steps_needed, 0
@@ -86,3 +94,28 @@ def test_summary_percentiles():
     assert s["p99_latency_s"] == pytest.approx(np.percentile(lat, 99))
     assert s["cell_updates"] == 5 * 100 * 5
     assert s["failed"] == 0
+
+
+def test_fast_oldest_marks_the_longest_admitted_within_the_cost_cap():
+    # cost per step = cells (2D FP64 weight 1): caps 250 -> the two oldest
+    rs = [FakeReq(k, 0.0, 1, 40 - 5 * k, cells=100) for k in range(5)]
+    for r in rs:
+        r.desc = r
+    eng = FakeEngine(capacity=100)
+    serve.serve_continuous(eng, rs, steps_per_poll=1, fast="oldest", fast_units=250.0)
+    first = [s for s, f in eng.fast_log if f][:2]
+    assert first == [0, 1]  # slots of requests 0 and 1 (admitted first)
+    assert all(r.result["status"] == 0 for r in rs)
+    # request 0 needs 40 steps; as a fast slot it finishes in 10 engine steps,
+    # before request 4 (20 steps, normal while the two oldest are present)
+    assert rs[0].result["done"] <= rs[4].result["done"]
+
+
+def test_fast_light_marks_cheap_requests_only():
+    rs = [FakeReq(0, 0.0, 1, 8, cells=1000), FakeReq(1, 0.0, 1, 8, cells=10),
+          FakeReq(2, 0.0, 1, 8, cells=20)]
+    for r in rs:
+        r.desc = r
+    eng = FakeEngine(capacity=100)
+    serve.serve_continuous(eng, rs, steps_per_poll=1, fast="light", fast_units=50.0)
+    assert sorted(s for s, f in eng.fast_log if f) == [1, 2]
