@@ -194,6 +194,36 @@ def scheme_orders(weno, wl, torch, n=N_GRID, steps=4, warmup=3):
     return out
 
 
+def configs_1d(weno, wl, torch):
+    """Configurations 1 and 2, each a full solve to its final time through
+    weno_solve (state resident on the GPU; wall time of the call, which
+    includes its launches and its final status read)."""
+    import time as _time
+    out = {}
+    for key, w, desc in (
+            ("C1_advection_N200_T2", wl.advection_sine(n=200),
+             "1D linear advection, N = 200, periodic [-1, 1], t = 2, FP64"),
+            ("C2_shock_density_N1600_T1.8", wl.shock_density(n=1600),
+             "1D Euler shock-density, N = 1600 on [-5, 5], t = 1.8, FP64"),
+            ("C2_riemann_batch_64xN1600_T0.4", wl.riemann_batch(nbatch=64, n=1600, seed=2),
+             "64 seeded 1D Euler Riemann problems, N = 1600 each, t = 0.4, FP64, one batch")):
+        d = weno.desc_for(w)
+        U0 = torch.from_numpy(np.ascontiguousarray(w["U"])).cuda()
+        ws = weno.workspace(d)
+        U = U0.clone()
+        weno.solve(d, U, w["t_final"], ws=ws)  # warm-up
+        U = U0.clone()
+        torch.cuda.synchronize()
+        t0 = _time.perf_counter()
+        _, n = weno.solve(d, U, w["t_final"], ws=ws)
+        el = _time.perf_counter() - t0
+        cells = d.nbatch * d.nx * d.ny
+        steps = int(np.max(n))
+        out[key] = {"workload": desc, "steps": steps, "seconds": el,
+                    "value": cells * float(np.sum(n)) / max(1, d.nbatch) / el, "unit": UNIT}
+    return out
+
+
 # admission budget of the engine: admitted solves' cost per step, in 2D FP64
 # cells (about 2 tiles per SM of 16x16 cells on 152 SMs, with a margin).
 WORK_BUDGET = 250e3
@@ -443,6 +473,7 @@ def main():
         result["precision_modes"] = precision_modes(weno, wl, torch)
         result["gpu_launches_precision_modes"] = 4 * 2 * (4 + 3)
     if not args.no_orders:
+        result["configs_1d"] = configs_1d(weno, wl, torch)
         result["scheme_orders"] = scheme_orders(weno, wl, torch)
         result["gpu_launches_scheme_orders"] = 4 * 4 * (4 + 3)
     if not args.no_serving and rank == 0:

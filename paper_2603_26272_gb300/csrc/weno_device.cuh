@@ -223,12 +223,19 @@ __device__ __forceinline__ double pair_flux(const ZA6Part &p, const ZA6Part &m) 
 // formed as v_{R-1} plus a correction (every c_k sums to 1); each indicator
 // beta_k = <f_k, B_k f_k> is evaluated on f_k minus its first entry (B_k
 // annihilates constants, so this is the same number with rounding relative to
-// the substencil's variation) and clamped at 0 against rounding; the weights
-// follow eqs. (16)-(21) with one division per candidate.
+// the substencil's variation) and clamped at 0 against rounding; tau from
+// c_tau on the stencil relative to v_{R-1} (c_tau sums to 0).  The weights
+// follow eqs. (16)-(22); for p = 1 without divisions per candidate, as in
+// za6: a_k = d_k (b_k + 4 tau) prod_{j != k} b_j after a power-of-two
+// rescale, in the "4 beta" units of za6 (b_k = 4 beta_k + 4 eps mu^2).
 // ---------------------------------------------------------------------------
 template <int R> struct OrderTab;
 
 template <> struct OrderTab<2> {
+  __device__ static double dn(int k) {  // d_k times its common denominator
+    const double v[3] = {1, 4, 1};
+    return v[k];
+  }
   __device__ static double ck(int k, int m) {
     const double c[3][2] = {{-1, 3}, {1, 1}, {3, -1}};
     return c[k][m] / 2.0;
@@ -247,6 +254,10 @@ template <> struct OrderTab<2> {
 };
 
 template <> struct OrderTab<4> {
+  __device__ static double dn(int k) {  // d_k times its common denominator
+    const double v[5] = {1, 16, 36, 16, 1};
+    return v[k];
+  }
   __device__ static double ck(int k, int m) {
     const double c[5][4] = {{-3, 13, -23, 25}, {1, -5, 13, 3}, {-1, 7, 7, -1}, {3, 13, -5, 1},
                             {25, -23, 13, -3}};
@@ -278,6 +289,10 @@ template <> struct OrderTab<4> {
 };
 
 template <> struct OrderTab<5> {
+  __device__ static double dn(int k) {  // d_k times its common denominator
+    const double v[6] = {1, 25, 100, 100, 25, 1};
+    return v[k];
+  }
   __device__ static double ck(int k, int m) {
     const double c[6][5] = {{12, -63, 137, -163, 137}, {-3, 17, -43, 77, 12},
                             {2, -13, 47, 27, -3},      {-3, 27, 47, -13, 2},
@@ -324,62 +339,125 @@ template <> struct OrderTab<5> {
   }
 };
 
+// Partial result of a reconstruction of order 2R: the flux is vc + num / den.
+struct RPart {
+  double vc, num, den;
+};
+
 template <int R, bool AI, bool P1>
-__device__ __forceinline__ double za_r(const double (&v)[2 * R], const ReconParams &P) {
+__device__ __forceinline__ RPart za_r(const double (&v)[2 * R], const ReconParams &P) {
   using Tb = OrderTab<R>;
   constexpr int N = 2 * R;
   const double vc = v[R - 1];
-  double beta[R + 1];
-  double bsum = 0.0;
+  double w[N];  // the stencil relative to v_{R-1}
 #pragma unroll
-  for (int k = 0; k <= R; ++k) {  // k = R: the downwind polynomial's beta_d
-    double g[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) g[m] = v[k + m] - v[k];
-    double s = 0.0;
-#pragma unroll
-    for (int a = 1; a < R; ++a) {
-      double row = 0.0;
-#pragma unroll
-      for (int b = 1; b < R; ++b) row = fma(Tb::B(k, a, b), g[b], row);
-      s = fma(g[a], row, s);
-    }
-    s = fmax(s, 0.0);
-    if (k < R) beta[k] = s;
-    bsum += s;
-  }
-  beta[R] = bsum * (1.0 / (R + 1));
-  double mean = 0.0;
-#pragma unroll
-  for (int j = 0; j < N; ++j) mean += v[j] - vc;
-  mean *= (1.0 / N);
-  double tr = 0.0;
-#pragma unroll
-  for (int j = 0; j < N; ++j) tr = fma(Tb::ctau(j), (v[j] - vc) - mean, tr);
-  const double tau = tr * tr;
+  for (int j = 0; j < N; ++j) w[j] = (j == R - 1) ? 0.0 : v[j] - vc;
   double e;
-  if (AI) {
-    double dev = 0.0;
+  if (AI) {  // mu from FP32 deviations, as in za6
+    float wf[N], m = 0.0f;
 #pragma unroll
-    for (int j = 0; j < N; ++j) dev += fabs((v[j] - vc) - mean);
-    const double mu = fma(dev, 1.0 / N, P.mu0s);
-    e = 0.25 * P.eps4 * (mu * mu);
+    for (int j = 0; j < N; ++j) {
+      wf[j] = (j == R - 1) ? 0.0f : __double2float_rn(w[j]);
+      m += wf[j];
+    }
+    m *= 1.0f / N;
+    float dev = 0.0f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) dev += fabsf(wf[j] - m);
+    const double sm = fma((double)dev, P.me * (6.0 / N), P.mo);  // sqrt(4 eps) mu
+    e = sm * sm;
   } else {
-    e = 0.25 * P.efix;
+    e = P.efix;
   }
-  double asum = 0.0, num = 0.0;
+  // b_k = 4 beta_k + e on f_k minus its first entry (symmetric form: each
+  // off-diagonal pair once); k = R is the downwind substencil's beta_d
+  double b[R + 1];
+  double bd = 0.0, bsum = 0.0;
 #pragma unroll
   for (int k = 0; k <= R; ++k) {
-    double G = tau / (beta[k] + e);
-    if (!P1) G = pow(G, P.p);
-    const double al = Tb::d(k) * (1.0 + G);
+    double g[R];
+#pragma unroll
+    for (int m = 1; m < R; ++m) g[m] = (k == R - 1) ? w[k + m] : w[k + m] - w[k];
+    double q = 0.0;
+#pragma unroll
+    for (int a = 1; a < R; ++a) {
+      double row = (4.0 * Tb::B(k, a, a)) * g[a];
+#pragma unroll
+      for (int c = a + 1; c < R; ++c) row = fma(8.0 * Tb::B(k, a, c), g[c], row);
+      q = fma(g[a], row, q);
+    }
+    q = fmax(q, 0.0) + e;  // the form is positive semidefinite; clamp its rounding
+    if (k < R) b[k] = q; else bd = q;
+    bsum += q;
+  }
+  b[R] = bsum * (1.0 / (R + 1));  // eq. (16): the mean, with e included once
+  double tr = 0.0;                // 2 (c_tau . f): T = 4 tau
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if (j != R - 1) tr = fma(2.0 * Tb::ctau(j), w[j], tr);
+  const double T0 = tr * tr;
+  double a[R + 1];
+  if (P1) {
+    unsigned long long mb = (unsigned long long)__double_as_longlong(bd);
+#pragma unroll
+    for (int k = 0; k < R; ++k) mb = max(mb, (unsigned long long)__double_as_longlong(b[k]));
+    mb = max(mb, (unsigned long long)__double_as_longlong(T0));
+    const int ex = (int)((mb >> 52) & 0x7FF);
+    if (AI) {  // exact exponent add, as in za6 (the b_k lie within ~1e-46 of the largest)
+      const int sh = (1023 - ex) << 20;
+#pragma unroll
+      for (int k = 0; k <= R; ++k)
+        b[k] = __hiloint2double(__double2hiint(b[k]) + sh, __double2loint(b[k]));
+    } else {
+      const double sc = __longlong_as_double((2046LL - ex) << 52);
+#pragma unroll
+      for (int k = 0; k <= R; ++k) b[k] *= sc;
+    }
+    const double T = T0 * __longlong_as_double((2046LL - ex) << 52);
+    // a_k = (b_k + T) prod_{j != k} b_j from prefix and suffix products
+    double pre[R + 1], suf[R + 1];
+    pre[0] = 1.0;
+    suf[R] = 1.0;
+#pragma unroll
+    for (int k = 1; k <= R; ++k) pre[k] = (k == 1) ? b[0] : pre[k - 1] * b[k - 1];
+#pragma unroll
+    for (int k = R - 1; k >= 0; --k) suf[k] = (k == R - 1) ? b[R] : suf[k + 1] * b[k + 1];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) {
+      const double pk = (k == 0) ? suf[0] : (k == R ? pre[R] : pre[k] * suf[k]);
+      a[k] = (b[k] + T) * pk;
+    }
+  } else {
+    const double T = T0;
+#pragma unroll
+    for (int k = 0; k <= R; ++k) a[k] = 1.0 + pow(T / b[k], P.p);
+  }
+  double num = 0.0, den = 0.0;
+#pragma unroll
+  for (int k = 0; k <= R; ++k) {
     double corr = 0.0;  // f^k - v_{R-1}
 #pragma unroll
-    for (int m = 0; m < R; ++m) corr = fma(Tb::ck(k, m), v[k + m] - vc, corr);
-    asum += al;
-    num = fma(al, corr, num);
+    for (int m = 0; m < R; ++m)
+      if (k + m != R - 1) corr = fma(Tb::ck(k, m), w[k + m], corr);
+    const double ak = (Tb::dn(k) == 1.0) ? a[k] : Tb::dn(k) * a[k];
+    num = fma(ak, corr, num);
+    den += ak;
   }
-  return vc + num / asum;
+  return RPart{vc, num, den};
+}
+
+// f^+ + f^- of one field from two reconstructions of order 2R.  Up to R = 4
+// the two denominators share one division; at R = 5 a single discontinuity
+// at the edge of the stencil leaves five flat substencils, whose products
+// reach ~1e-170 (in the rescaled units), and the product of two such
+// denominators would underflow, so each keeps its own division there.
+template <int R>
+__device__ __forceinline__ double pair_flux_r(const RPart &p, const RPart &m) {
+  if (R <= 4) {
+    const double q = fma(p.num, m.den, m.num * p.den) / (p.den * m.den);
+    return (p.vc + m.vc) + q;
+  }
+  return (p.vc + p.num / p.den) + (m.vc + m.num / m.den);
 }
 
 // ---------------------------------------------------------------------------

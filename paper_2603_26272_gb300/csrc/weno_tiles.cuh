@@ -317,10 +317,10 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
         h4 = pair_flux(za6<AI, P1>(p4[0], p4[1], p4[2], p4[3], p4[4], p4[5], rp4),
                        za6<AI, P1>(m4[0], m4[1], m4[2], m4[3], m4[4], m4[5], rp4));
       } else {
-        h1 = za_r<R, AI, P1>(p1, rp4) + za_r<R, AI, P1>(m1, rp4);
-        h2 = za_r<R, AI, P1>(p2, rp2) + za_r<R, AI, P1>(m2, rp2);
-        h3 = za_r<R, AI, P1>(p3, rp2) + za_r<R, AI, P1>(m3, rp2);
-        h4 = za_r<R, AI, P1>(p4, rp4) + za_r<R, AI, P1>(m4, rp4);
+        h1 = pair_flux_r<R>(za_r<R, AI, P1>(p1, rp4), za_r<R, AI, P1>(m1, rp4));
+        h2 = pair_flux_r<R>(za_r<R, AI, P1>(p2, rp2), za_r<R, AI, P1>(m2, rp2));
+        h3 = pair_flux_r<R>(za_r<R, AI, P1>(p3, rp2), za_r<R, AI, P1>(m3, rp2));
+        h4 = pair_flux_r<R>(za_r<R, AI, P1>(p4, rp4), za_r<R, AI, P1>(m4, rp4));
       }
     }
     double F0, F1, F2, F3;
@@ -472,7 +472,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             h = pair_flux(za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp),
                           za6<AI, P1>(mm[0], mm[1], mm[2], mm[3], mm[4], mm[5], rp));
           else
-            h = za_r<R, AI, P1>(pp, rp) + za_r<R, AI, P1>(mm, rp);
+            h = pair_flux_r<R>(za_r<R, AI, P1>(pp, rp), za_r<R, AI, P1>(mm, rp));
         }
         fl[f][0] = 0.5 * h;
       } else {
@@ -521,9 +521,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             h3 = pair_flux(za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp4),
                            za6<AI, P1>(m3[0], m3[1], m3[2], m3[3], m3[4], m3[5], rp4));
           } else {
-            h1 = za_r<R, AI, P1>(p1, rp4) + za_r<R, AI, P1>(m1, rp4);
-            h2 = za_r<R, AI, P1>(p2, rp2) + za_r<R, AI, P1>(m2, rp2);
-            h3 = za_r<R, AI, P1>(p3, rp4) + za_r<R, AI, P1>(m3, rp4);
+            h1 = pair_flux_r<R>(za_r<R, AI, P1>(p1, rp4), za_r<R, AI, P1>(m1, rp4));
+            h2 = pair_flux_r<R>(za_r<R, AI, P1>(p2, rp2), za_r<R, AI, P1>(m2, rp2));
+            h3 = pair_flux_r<R>(za_r<R, AI, P1>(p3, rp4), za_r<R, AI, P1>(m3, rp4));
           }
         }
         double F0, F1, F2;
@@ -605,10 +605,10 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
     // 4 = 16x8 / 64 / 6, and two shapes whose face count is a multiple of
     // the block's threads, so every warp computes the same number of faces:
     // 5 = 20x12 / 128 / 3 (512 faces), 6 = 26x14 / 128 / 3 (768 faces).
-    // The other orders use 16x16 / 128 / 2 only (their wider halo and
-    // stencil).
-    if constexpr (R != 3) {
-      return launch_2d<16, 16, 128, 2, AI, P1, PREC, R>(a, s);
+    // The other orders use 16x16 / 128 only, 3 blocks per SM at r = 2 and 2
+    // at r = 4, 5 (their wider stencils need more registers).
+    if constexpr (R != 3) {  // r = 2 fits the 168-register cap of 3 blocks per SM
+      return launch_2d<16, 16, 128, (R == 2 ? 3 : 2), AI, P1, PREC, R>(a, s);
     } else {
       switch (a.tile_variant) {
         case 1: return launch_2d<16, 16, 128, 2, AI, P1, PREC>(a, s);
