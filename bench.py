@@ -229,7 +229,7 @@ def configs_1d(weno, wl, torch):
 WORK_BUDGET = 250e3
 
 
-def serving(n_requests=100, seed=5, loads=(1.0, 1.25)):
+def serving(n_requests=100, seed=5, loads=(1.0, 1.25), mix="small"):
     """Configuration 5, scaled to about a minute: a seeded stream of mixed
     1D/2D, FP64/FP32-reconstruction solves.  The offered Poisson rate is set
     to `loads` x the one-at-a-time capacity (measured first on the same GPU);
@@ -237,7 +237,10 @@ def serving(n_requests=100, seed=5, loads=(1.0, 1.25)):
     and by the continuous-batching engine."""
     import torch
     from paper_2603_26272_gb300 import serve
-    sides, n1d, steps = (128, 192, 256), (256, 16384), (100, 300)
+    if mix == "full":
+        sides, n1d, steps = (128, 192, 256, 384, 512, 768, 1024), (256, 16384), (100, 1000)
+    else:
+        sides, n1d, steps = (128, 192, 256), (256, 16384), (100, 300)
     reqs = serve.make_requests(n_requests, seed=seed, rate=None, sides_2d=sides, n1d=n1d,
                                steps=steps)
     serve.serve_one_at_a_time(reqs)  # calibration: service times back to back
@@ -354,6 +357,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-orders", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=100)
+    ap.add_argument("--serving-mix", choices=["small", "full"], default="small",
+                    help="small: 2D sides 128-256, 100-300 steps (about a minute); full: the "
+                         "configured sides 128-1024 and 100-1000 steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -449,6 +455,7 @@ def main():
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "stage_updates_per_s": 3 * value,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "2D Euler %dx%d four-quadrant Riemann data (seed %d, rho,p~U[0.1,1.5], "
@@ -478,7 +485,7 @@ def main():
         result["gpu_launches_scheme_orders"] = 4 * 4 * (4 + 3)
     if not args.no_serving and rank == 0:
         log("serving stream ...")
-        result["serving"] = serving(args.serving_requests)
+        result["serving"] = serving(args.serving_requests, mix=args.serving_mix)
     if rank == 0 and not args.no_cpu_baseline:
         log("timing the CPU oracle on the host cores ...")
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

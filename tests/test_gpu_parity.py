@@ -331,3 +331,25 @@ def test_tile_variants_are_bitwise_identical(prec, monkeypatch):
     for _ in range(3):
         weno.step(d, U)
     assert np.array_equal(U.cpu().numpy(), outs[0])
+
+
+def test_advection_sixth_order_on_gpu():
+    """Configuration 1's convergence sweep on the GPU path: u0 = sin(pi x -
+    sin(pi x)/pi) on periodic [-1, 1] to t = 2 with dt = 0.5 dx^2 (so the
+    RK3 error is O(dx^6)); the error against the exact solution falls at
+    sixth order (Section 3.1, Table 2)."""
+    errs = []
+    for n in (20, 40, 80, 160):
+        w = wl.advection_sine(n=n)
+        d = weno.desc_for(w)
+        dx = w["dx"]
+        steps = int(np.ceil(2.0 / (0.5 * dx * dx) - 1e-12))
+        dt = 2.0 / steps
+        U = to_gpu(w["U"])
+        ws = weno.workspace(d)
+        for _ in range(steps):
+            weno.step(d, U, dt=dt, ws=ws, sync=False)
+        weno.sync_status(d, ws)
+        errs.append(np.abs(U.cpu().numpy()[0, 0, 0] - w["exact"](w["x"], 2.0)).max())
+    orders = [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+    assert orders[-1] > 5.5 and orders[-2] > 5.0, (errs, orders)
