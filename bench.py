@@ -311,6 +311,18 @@ def cpu_baseline(seconds, window=256):
                       % (window, window, steps, el)}
 
 
+def job_timing(elapsed_ms, world, cells, steps, dist=None, device=None):
+    """Whole-job throughput of N replicas: the slowest rank's timed region
+    (all_reduce MAX over ranks) and every rank's cell-updates over it."""
+    t_max = float(elapsed_ms)
+    if dist is not None:
+        import torch
+        tt = torch.tensor([t_max], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return t_max, world * cells * steps / (t_max / 1e3)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -427,14 +439,9 @@ def main():
         dist.barrier()
     elapsed_ms = start.elapsed_time(end)
     weno.sync_status(d, ws)
-    t_max = elapsed_ms
-    if dist:
-        tt = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-
     cells = n * n
-    value = world * cells * args.steps / (t_max / 1e3)
+    t_max, value = job_timing(elapsed_ms, world, cells, args.steps, dist,
+                              torch.device("cuda", local) if dist else None)
     ms_step = t_max / args.steps
 
     # end to end: the public host-buffer call, H2D + step + D2H per step
