@@ -75,9 +75,12 @@ typedef struct weno_desc {
   double cfl;         /* CFL number of the time step rule                         */
   double eps;         /* sensitivity epsilon of eq. (21); with ai = 1, >= 1e-250  */
   double mu0;         /* mu_0 of eq. (22); with ai = 1, >= 1e-100                 */
-  double p;           /* power parameter p of eq. (21), >= 1                      */
+  double p;           /* power parameter p of eq. (21), > 0 (the paper: 1, 3/2, 2) */
   int32_t ai;         /* 1: affine-invariant descaler mu[f] of eq. (22); 0: mu = 1 */
-  int32_t precision;  /* WENO_PREC_FP64 (FP32_RECON is reserved)                  */
+  int32_t precision;  /* WENO_PREC_FP64, or WENO_PREC_FP32_RECON: the indicators, */
+                      /* weights and candidates of eqs. (11)-(22) in FP32 on the  */
+                      /* mu-normalised stencil differences (needs ai = 1, order   */
+                      /* 6); projections, fluxes and RK accumulation stay FP64    */
   int32_t alpha_mode; /* WENO_ALPHA_FIELD: GLF speed per characteristic field;    */
                       /* WENO_ALPHA_SINGLE: one speed max|u|+c for all fields     */
   int32_t order;      /* 2r, the order of the central-upwind scheme: 0 or 6 =      */
