@@ -507,16 +507,33 @@ __device__ __forceinline__ float za6_f32(float e0, float e1, float e2, float e3,
   const float B3 = 0.25f * ((B0 + B1) + (B2 + Bd));
   const float r5 = fmaf(3.0f, s1 - s2, s3 - s0);
   const float T = 4.0f * (r5 * r5);
-  float g0 = T / (B0 + P.eps4), g1 = T / (B1 + P.eps4), g2 = T / (B2 + P.eps4),
-        g3 = T / (B3 + P.eps4);
-  if (!P1) {
-    g0 = powf(g0, P.p);
-    g1 = powf(g1, P.p);
-    g2 = powf(g2, P.p);
-    g3 = powf(g3, P.p);
+  const float b0 = B0 + P.eps4, b1 = B1 + P.eps4, b2 = B2 + P.eps4, b3 = B3 + P.eps4;
+  float a0w, a1w, a2w, a3w;
+  if (P1) {
+    a0w = 1.0f + T / b0;
+    a1w = 9.0f * (1.0f + T / b1);
+    a2w = 9.0f * (1.0f + T / b2);
+    a3w = 1.0f + T / b3;
+  } else {
+    // (T / b_k)^p overflows FP32 next to a flat substencil (T / eps32 ~ 1e33),
+    // so with b_min the smallest b_k every alpha_k is taken times
+    // (b_min / T)^p when T > b_min: alpha_k ~ d_k ((b_min/T)^p + (b_min/b_k)^p),
+    // the same weights, and no term above 1.
+    const float bmin = fminf(fminf(b0, b1), fminf(b2, b3));
+    const float q0 = powf(bmin / b0, P.p), q1 = powf(bmin / b1, P.p),
+                q2 = powf(bmin / b2, P.p), q3 = powf(bmin / b3, P.p);
+    float base = 1.0f, M = 0.0f;
+    if (T <= bmin) {
+      M = powf(T / bmin, P.p);  // alpha_k = d_k (1 + M q_k)
+    } else {
+      base = powf(bmin / T, P.p);  // alpha_k ~ d_k ((b_min/T)^p + q_k)
+      M = 1.0f;
+    }
+    a0w = fmaf(M, q0, base);
+    a1w = 9.0f * fmaf(M, q1, base);
+    a2w = 9.0f * fmaf(M, q2, base);
+    a3w = fmaf(M, q3, base);
   }
-  const float a0w = 1.0f + g0, a1w = 9.0f * (1.0f + g1), a2w = 9.0f * (1.0f + g2),
-              a3w = 1.0f + g3;
   const float is = 1.0f / ((a0w + a1w) + (a2w + a3w));
   const float r0 = fmaf(5.0f, d1, -2.0f * d0);
   const float r1 = fmaf(2.0f, d2, d1);

@@ -110,3 +110,17 @@ def test_fp32_recon_needs_affine_invariant_weights():
     with pytest.raises(weno.WenoError) as ei:
         weno.rhs(d, torch.zeros((1, 3, 1, 64), dtype=torch.float64, device="cuda"))
     assert ei.value.code == weno.WENO_ERR_ARG
+
+
+@pytest.mark.parametrize("p", [1.5, 2.0])
+def test_fp32_recon_power_parameter_next_to_flat_substencils(p):
+    """With p > 1, (tau / beta_k)^p of a flat substencil next to a jump is far
+    beyond FP32's range; the weights are formed relative to the smallest
+    indicator, so the mode stays finite and close to the FP64 oracle."""
+    w = wl.quadrant_2d(n=64, seed=4)
+    d = weno.desc_for(w, precision="fp32_recon", p=p)
+    g = oracle.make_grid(ndim=2, nx=64, ny=64, dx=(d.x1 - d.x0) / 64, dy=(d.y1 - d.y0) / 64, p=p)
+    L_o = oracle.rhs(g, w["U"])
+    L_g = weno.rhs(d, torch.from_numpy(np.ascontiguousarray(w["U"])).cuda()).cpu().numpy()
+    assert np.isfinite(L_g).all()
+    assert rel_linf(L_g, L_o) <= STAGE_TOL_F32
