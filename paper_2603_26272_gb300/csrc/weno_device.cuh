@@ -120,10 +120,14 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 // eps mu^2 with eps = 1e-40, which matters only for a substencil whose
 // indicator is below ~1e-30 mu^2, where a relative error of 1e-7 in mu moves
 // Gamma_k by the same relative amount and the weights by less than 1e-30.
+// Differences beyond FP32's range (a sum that overflows) take the same sum in
+// FP64; the rescale below relies on mu being right to within that 1e-7.
 // ---------------------------------------------------------------------------
 struct ZA6Part {
   double v2, num, den;  // f = v2 + num / (6 den)
 };
+
+
 
 template <bool AI, bool P1>
 __device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v3, double v4,
@@ -141,11 +145,17 @@ __device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v
     const float f0 = __double2float_rn(d0), f1 = __double2float_rn(d1),
                 f2 = __double2float_rn(d2), f3 = __double2float_rn(d3),
                 f4 = __double2float_rn(d4);
-    const float a0 = -(f0 + f1), a1 = -f1, a3 = f2, a4 = f2 + f3, a5 = a4 + f4;
-    const float m = ((a0 + a1) + (a3 + a4) + a5) * (1.0f / 6.0f);
-    const float dev = fabsf(a0 - m) + fabsf(a1 - m) + fabsf(m) + fabsf(a3 - m) + fabsf(a4 - m) +
-                      fabsf(a5 - m);
-    const double sm = fma((double)dev, P.me, P.mo);  // sqrt(4 eps) mu
+    const float fa0 = -(f0 + f1), fa1 = -f1, fa3 = f2, fa4 = f2 + f3, fa5 = fa4 + f4;
+    const float fm = ((fa0 + fa1) + (fa3 + fa4) + fa5) * (1.0f / 6.0f);
+    const float devf = fabsf(fa0 - fm) + fabsf(fa1 - fm) + fabsf(fm) + fabsf(fa3 - fm) +
+                       fabsf(fa4 - fm) + fabsf(fa5 - fm);
+    double dev = (double)devf;
+    if (!(devf <= 3.0e38f)) {  // differences beyond FP32's range: the same sum in FP64
+      const double a0 = -(d0 + d1), a1 = -d1, a3 = d2, a4 = d2 + d3, a5 = a4 + d4;
+      const double m = ((a0 + a1) + (a3 + a4) + a5) * (1.0 / 6.0);
+      dev = fabs(a0 - m) + fabs(a1 - m) + fabs(m) + fabs(a3 - m) + fabs(a4 - m) + fabs(a5 - m);
+    }
+    const double sm = fma(dev, P.me, P.mo);  // sqrt(4 eps) mu
     e = sm * sm;
   } else {
     e = P.efix;
@@ -353,18 +363,28 @@ __device__ __forceinline__ RPart za_r(const double (&v)[2 * R], const ReconParam
 #pragma unroll
   for (int j = 0; j < N; ++j) w[j] = (j == R - 1) ? 0.0 : v[j] - vc;
   double e;
-  if (AI) {  // mu from FP32 deviations, as in za6
-    float wf[N], m = 0.0f;
+  if (AI) {  // mu from FP32 deviations, as in za6 (FP64 beyond FP32's range)
+    float wf[N], mf = 0.0f;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       wf[j] = (j == R - 1) ? 0.0f : __double2float_rn(w[j]);
-      m += wf[j];
+      mf += wf[j];
     }
-    m *= 1.0f / N;
-    float dev = 0.0f;
+    mf *= 1.0f / N;
+    float df = 0.0f;
 #pragma unroll
-    for (int j = 0; j < N; ++j) dev += fabsf(wf[j] - m);
-    const double sm = fma((double)dev, P.me * (6.0 / N), P.mo);  // sqrt(4 eps) mu
+    for (int j = 0; j < N; ++j) df += fabsf(wf[j] - mf);
+    double dev = (double)df;
+    if (!(df <= 3.0e38f)) {
+      dev = 0.0;
+      double m = 0.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) m += w[j];
+      m *= 1.0 / N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) dev += fabs(w[j] - m);
+    }
+    const double sm = fma(dev, P.me * (6.0 / N), P.mo);  // sqrt(4 eps) mu
     e = sm * sm;
   } else {
     e = P.efix;

@@ -353,3 +353,24 @@ def test_advection_sixth_order_on_gpu():
         errs.append(np.abs(U.cpu().numpy()[0, 0, 0] - w["exact"](w["x"], 2.0)).max())
     orders = [np.log2(a / b) for a, b in zip(errs, errs[1:])]
     assert orders[-1] > 5.5 and orders[-2] > 5.0, (errs, orders)
+
+
+@pytest.mark.parametrize("scale_exp", [-60, 200, 400])
+@pytest.mark.parametrize("order", [6, 4, 10])
+def test_extreme_magnitudes(scale_exp, order):
+    """The Euler right-hand side is homogeneous of degree 1 in U (u, c are
+    unchanged, p and the fluxes scale) and the affine-invariant weights are
+    scale-free, so L(2^k U) = 2^k L(U).  At 2^400 the indicators are ~2^800:
+    the exponent rescale of the weights must keep every product finite; at
+    2^-60 they are ~2^-120.  Checked against the oracle at the scaled data
+    and against the scaled unscaled result."""
+    w = wl.quadrant_2d(n=48, seed=9)
+    c = 2.0 ** scale_exp
+    d = _desc(w, {"order": order})
+    g = ora_grid(w, d, order=order)
+    U = np.ascontiguousarray(w["U"])
+    L1 = weno.rhs(d, to_gpu(U)).cpu().numpy()
+    Lc = weno.rhs(d, to_gpu(U * c)).cpu().numpy()
+    assert np.isfinite(Lc).all()
+    assert rel_err(Lc / c, L1) <= 1e-12
+    assert rel_err(Lc, oracle.rhs(g, U * c)) <= STAGE_TOL
