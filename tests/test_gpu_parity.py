@@ -374,3 +374,44 @@ def test_extreme_magnitudes(scale_exp, order):
     assert np.isfinite(Lc).all()
     assert rel_err(Lc / c, L1) <= 1e-12
     assert rel_err(Lc, oracle.rhs(g, U * c)) <= STAGE_TOL
+
+
+def test_gpu_invariants_mirror_reduction_transpose():
+    """Invariants of the GPU path itself (Section 8(c) pins, here on the GPU):
+    mirror symmetry x -> -x, u -> -u in 1D; 2D data independent of y give
+    the 1D right-hand side in every row and a zero y-momentum change; the
+    x <-> y transpose of 2D data (swapping the momenta) transposes L(U)."""
+    w = wl.shock_density(n=96)
+    d = weno.desc_for(w)
+    U = np.ascontiguousarray(w["U"])
+    L = weno.rhs(d, to_gpu(U)).cpu().numpy()
+    Um = U[:, :, :, ::-1].copy()
+    Um[:, 1] *= -1.0
+    Lm = weno.rhs(d, to_gpu(Um)).cpu().numpy()[:, :, :, ::-1].copy()
+    Lm[:, 1] *= -1.0
+    assert np.abs(Lm - L).max() <= 1e-13 * np.abs(L).max()
+
+    w1 = wl.shock_density(n=80)
+    d1 = weno.desc_for(w1)
+    L1 = weno.rhs(d1, to_gpu(w1["U"])).cpu().numpy()
+    ny = 7
+    U2 = np.zeros((1, 4, ny, 80))
+    U2[0, 0] = w1["U"][0, 0, 0]
+    U2[0, 1] = w1["U"][0, 1, 0]
+    U2[0, 3] = w1["U"][0, 2, 0]
+    for bcy in ("transmissive", "periodic"):
+        d2 = weno.make_desc(system="euler", ndim=2, nx=80, ny=ny, x0=d1.x0, x1=d1.x1, y0=0.0,
+                            y1=0.37 * ny, bc_x="transmissive", bc_y=bcy)
+        L2 = weno.rhs(d2, to_gpu(U2)).cpu().numpy()
+        scale = np.abs(L1).max()
+        for j in range(ny):
+            assert np.abs(L2[0, [0, 1, 3], j, :] - L1[0, :, 0, :]).max() <= 1e-13 * scale
+        assert np.abs(L2[0, 2]).max() <= 1e-13 * scale
+
+    q = wl.quadrant_2d(n=40, seed=5)
+    dq = weno.desc_for(q)
+    Uq = np.ascontiguousarray(q["U"])
+    Lq = weno.rhs(dq, to_gpu(Uq)).cpu().numpy()
+    UT = np.ascontiguousarray(Uq[:, [0, 2, 1, 3]].transpose(0, 1, 3, 2))
+    LT = weno.rhs(dq, to_gpu(UT)).cpu().numpy()[:, [0, 2, 1, 3]].transpose(0, 1, 3, 2)
+    assert np.abs(LT - Lq).max() <= 1e-13 * np.abs(Lq).max()
