@@ -672,14 +672,26 @@ __device__ __forceinline__ void backproject4(const FaceState &f, double h1, doub
 // 1D Euler (rho, m, E): R = [(1, u-c, H-uc), (1, u, u^2/2), (1, u+c, H+uc)],
 // L rows 1/2 (b2 + u/c, -(b1 u + 1/c), b1), (1-b2, b1 u, -b1),
 // 1/2 (b2 - u/c, -(b1 u - 1/c), b1); fields scaled by k = (4, 2, 4).
+// (Written with explicit FMAs only, so the compiler has nothing to contract
+// and project3_field below computes every field bit for bit as project3.)
 __device__ __forceinline__ void project3(const FaceState &f, double r, double m, double E,
                                          double &w1, double &w2, double &w3) {
   const double s = fma(f.un, m, -E);
   const double z = fma(f.b2, r, -(f.b1 * s));
-  const double tc = fma(f.un, r, -m) * f.ic;
-  w1 = z + tc;
-  w3 = z - tc;
+  const double t = fma(f.un, r, -m);
+  w1 = fma(t, f.ic, z);
+  w3 = fma(-t, f.ic, z);
   w2 = r - z;
+}
+
+// Field q of project3 alone (the same operations as its q-th output).
+__device__ __forceinline__ double project3_field(const FaceState &f, int q, double r, double m,
+                                                 double E) {
+  const double s = fma(f.un, m, -E);
+  const double z = fma(f.b2, r, -(f.b1 * s));
+  if (q == 1) return r - z;
+  const double t = fma(f.un, r, -m);
+  return fma(q == 0 ? t : -t, f.ic, z);
 }
 
 __device__ __forceinline__ void backproject3(const FaceState &f, double h1, double h2, double h3,

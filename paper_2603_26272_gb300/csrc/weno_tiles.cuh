@@ -393,22 +393,31 @@ __global__ void __launch_bounds__(NT, MINB) k_euler2d(const StageArgs a) {
 // kT1 = 127 cells, 128 faces, one face per thread.
 // Planes: 0 rho, 1 m, 2 E, 3 u, 4 H, 5 sqrt(rho), 6-8 F  (advection: 0 u).
 // ---------------------------------------------------------------------------
-template <int NC, int T, int R = 3>
+template <int NC, int T, int R = 3, int LANES = 1>
 constexpr size_t smem_line1d() {
-  return sizeof(double) * (((NC == 3) ? 9 : 2) * (T + 2 * R) + (T + 1) * NC);
+  return sizeof(double) * (((NC == 3) ? 9 : 2) * (T + 2 * R) + (T + 1) * NC +
+                           (LANES > 1 ? (T + 1) * NC : 0));
 }
 
-// One tile of T cells (T + 1 faces, one per thread; blockDim = T + 1) of a
-// 1D stage with a stencil of half-width R (order 2R).  sm: dynamic shared
-// memory of smem_line1d<NC, T, R>() bytes.
-template <int NC, bool AI, bool P1, int PREC, int T, int R = 3>
+// One tile of T cells (T + 1 faces) of a 1D stage with a stencil of
+// half-width R (order 2R).  LANES threads share a face: 1 (blockDim = T + 1,
+// the throughput layout), or -- for problems too small to fill the GPU, where
+// a stage's time is one thread's chain of FP64 operations -- 3 for Euler (one
+// characteristic field each; blockDim >= 3 (T + 1)) and 2 for a scalar (the
+// positive and the negative flux; blockDim >= 2 (T + 1)).  Every lane layout
+// runs the same arithmetic per field, so the results are bitwise identical.
+// sm: dynamic shared memory of smem_line1d<NC, T, R, LANES>() bytes.
+template <int NC, bool AI, bool P1, int PREC, int T, int R = 3, int LANES = 1>
 __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, long long tile,
                                             bool zeroing_block, double *sm) {
   static_assert(R == 3 || PREC == 0, "FP32 reconstruction is sixth order only");
+  static_assert(LANES == 1 || (R == 3 && LANES == (NC == 3 ? 3 : 2) && (NC == 3 || PREC == 0)),
+                "lane layouts: 3 per face for Euler, 2 for a scalar in FP64, sixth order");
   constexpr int REG = T + 2 * R, N = 2 * R;
   constexpr int NP = (NC == 3) ? 9 : 2;
   double(*pl)[REG] = reinterpret_cast<double(*)[REG]>(sm);
   double(*fl)[NC] = reinterpret_cast<double(*)[NC]>(sm + NP * REG);
+  double *const hb = sm + NP * REG + (T + 1) * NC;  // LANES > 1: per-field fluxes
   const long long i0 = tile * T;
   double dt;
   if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
@@ -445,7 +454,76 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
   }
   __syncthreads();
 
-  {
+  if constexpr (LANES == 3) {
+    // one characteristic field per thread; the field-0 thread back-projects
+    const int f = tid / 3, q = tid - 3 * f;
+    const bool act = (f <= T) && (i0 + f - 1 < nx);
+    FaceState fs;
+    if (act) {
+      const int kL = f + 2, kR = f + 3;
+      if (!roe_face(pl[5][kL], pl[3][kL], 0.0, pl[4][kL], pl[5][kR], pl[3][kR], 0.0, pl[4][kR],
+                    gm1, fs) && q == 0)
+        record_status(a.status, 3, a.stage, b, 0, i0 + f);
+      const unsigned long long *al = a.alpha_in + b * 8;
+      double A = bits2d(al[q]);
+      if (a.alpha_single) A = fmax(fmax(bits2d(al[0]), bits2d(al[1])), bits2d(al[2]));
+      double h;
+      if constexpr (PREC == 1) {
+        double W[6], G[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const int k = f + j;
+          W[j] = project3_field(fs, q, pl[0][k], pl[1][k], pl[2][k]);
+          G[j] = project3_field(fs, q, pl[6][k], pl[7][k], pl[8][k]);
+        }
+        h = field_flux_f32<P1>(W, G, A, make_r32(a));
+      } else {
+        const ReconParams rp = make_rp(a, q == 1 ? 2.0 : 4.0);
+        double pp[6], mm[6];  // f^- mirrored
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const int k = f + j;
+          const double w = project3_field(fs, q, pl[0][k], pl[1][k], pl[2][k]);
+          const double g = project3_field(fs, q, pl[6][k], pl[7][k], pl[8][k]);
+          pp[j] = fma(A, w, g);
+          mm[5 - j] = fma(-A, w, g);
+        }
+        h = pair_flux(za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp),
+                      za6<AI, P1>(mm[0], mm[1], mm[2], mm[3], mm[4], mm[5], rp));
+      }
+      hb[3 * f + q] = h;
+    }
+    __syncthreads();
+    if (act && q == 0) {
+      double F0, F1, F2;
+      backproject3(fs, hb[3 * f], hb[3 * f + 1], hb[3 * f + 2], F0, F1, F2);
+      fl[f][0] = F0;
+      fl[f][1] = F1;
+      fl[f][2] = F2;
+    }
+  } else if constexpr (LANES == 2) {
+    // the positive (even lane) and the mirrored negative flux (odd lane) of a
+    // scalar face; the partial sums meet by a lane shuffle
+    const int f = tid >> 1, sgn = tid & 1;
+    const bool act = (f <= T) && (i0 + f - 1 < nx);
+    ZA6Part part = {0.0, 0.0, 1.0};
+    if (act) {
+      const double A = scalar_alpha_of(a.system, a.adv_speed, a.ustar, a.alpha_in + b * 8);
+      const double As = sgn ? -A : A;
+      const ReconParams rp = make_rp(a, 2.0);
+      double v[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int k = sgn ? f + 5 - j : f + j;
+        v[j] = fma(As, pl[0][k], pl[1][k]);
+      }
+      part = za6<AI, P1>(v[0], v[1], v[2], v[3], v[4], v[5], rp);
+    }
+    const ZA6Part other = {__shfl_xor_sync(0xffffffffu, part.v2, 1),
+                           __shfl_xor_sync(0xffffffffu, part.num, 1),
+                           __shfl_xor_sync(0xffffffffu, part.den, 1)};
+    if (act && sgn == 0) fl[f][0] = 0.5 * pair_flux(part, other);
+  } else {
     const int f = tid;  // face between cells i0+f-1 and i0+f; stencil f..f+2R-1
     if (f <= T && i0 + f - 1 < nx) {
       if (NC == 1) {
@@ -584,6 +662,30 @@ __global__ void __launch_bounds__(kThreads1D) k_line1d(const StageArgs a) {
                                         blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
 }
 
+// Latency layout of small 1D problems: 128 threads, 3 per face for Euler
+// (41 cells a tile) or 2 per face for a scalar (63 cells).
+__host__ __device__ constexpr int kT1Lanes(int nc) { return nc == 3 ? 41 : 63; }
+
+template <int NC, bool AI, bool P1, int PREC>
+__global__ void __launch_bounds__(kThreads1D) k_line1d_lanes(const StageArgs a) {
+  extern __shared__ double sm[];
+  line1d_tile<NC, AI, P1, PREC, kT1Lanes(NC), 3, (NC == 3 ? 3 : 2)>(
+      a, blockIdx.y, blockIdx.x, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
+}
+
+// Multiprocessors of the current device (asked once per process and device).
+inline int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 152;
+  }
+  return cached[dev];
+}
+
 template <int TX, int TY, int NT, int MINB, bool AI, bool P1, int PREC, int R = 3>
 cudaError_t launch_2d(const StageArgs &a, cudaStream_t s) {
   const size_t smem = smem_euler2d<TX, TY, R>();
@@ -622,6 +724,22 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
     }
   }
   const long long tiles = (a.nx + kT1 - 1) / kT1;
+  if constexpr (R == 3) {
+    // A problem of fewer tiles than the GPU has SMs is bound by the length
+    // of one thread's chain of FP64 operations: spread each face over
+    // several threads (and the problem over more blocks) instead.
+    if (tiles * a.nbatch < (long long)sm_count() && (a.nc == 3 || PREC == 0)) {
+      const int tl1 = a.nc == 3 ? kT1Lanes(3) : kT1Lanes(1);
+      dim3 g2((unsigned)((a.nx + tl1 - 1) / tl1), (unsigned)a.nbatch, 1);
+      if (a.nc == 3)
+        k_line1d_lanes<3, AI, P1, PREC>
+            <<<g2, kThreads1D, smem_line1d<3, kT1Lanes(3), 3, 3>(), s>>>(a);
+      else if constexpr (PREC == 0)
+        k_line1d_lanes<1, AI, P1, PREC>
+            <<<g2, kThreads1D, smem_line1d<1, kT1Lanes(1), 3, 2>(), s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid((unsigned)tiles, (unsigned)a.nbatch, 1);
   if (a.nc == 3)
     k_line1d<3, AI, P1, PREC, R><<<grid, kThreads1D, smem_line1d<3, kT1, R>(), s>>>(a);

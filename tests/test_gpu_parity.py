@@ -415,3 +415,27 @@ def test_gpu_invariants_mirror_reduction_transpose():
     UT = np.ascontiguousarray(Uq[:, [0, 2, 1, 3]].transpose(0, 1, 3, 2))
     LT = weno.rhs(dq, to_gpu(UT)).cpu().numpy()[:, [0, 2, 1, 3]].transpose(0, 1, 3, 2)
     assert np.abs(LT - Lq).max() <= 1e-13 * np.abs(Lq).max()
+
+
+@pytest.mark.parametrize("name", ["shock_density", "advection", "burgers"])
+def test_small_1d_lane_layout_is_bitwise_the_batched_one(name):
+    """A 1D problem of fewer tiles than the GPU has SMs runs with several
+    threads per face; a batch of many copies of it runs one thread per face.
+    Both compute the same operations per field, so every copy equals the
+    single problem bit for bit (right-hand side and a full step)."""
+    w = {"shock_density": wl.shock_density(n=1600), "advection": wl.advection_sine(n=200),
+         "burgers": wl.burgers_sine(n=300)}[name]
+    d1 = weno.desc_for(w)
+    U1 = np.ascontiguousarray(w["U"])
+    copies = 256 if d1.ncomp == 1 else 24
+    wb = dict(w)
+    wb["U"] = np.ascontiguousarray(np.repeat(U1, copies, axis=0))
+    db = weno.desc_for(wb)
+    L1 = weno.rhs(d1, to_gpu(U1)).cpu().numpy()
+    Lb = weno.rhs(db, to_gpu(wb["U"])).cpu().numpy()
+    for c in (0, copies // 2, copies - 1):
+        assert np.array_equal(Lb[c], L1[0])
+    A, B = to_gpu(U1), to_gpu(wb["U"])
+    weno.step(d1, A)
+    weno.step(db, B)
+    assert np.array_equal(B.cpu().numpy()[copies - 1], A.cpu().numpy()[0])
