@@ -14,7 +14,7 @@ struct DevStatus {
 };
 
 // 2D tile variants of the single-problem stage kernel (see launch_stage_t).
-constexpr int kTileVariants = 7;
+constexpr int kTileVariants = 9;
 
 // Everything one stage launch needs (passed by value).
 struct StageArgs {

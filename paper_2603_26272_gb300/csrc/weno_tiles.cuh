@@ -707,6 +707,9 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
     // 4 = 16x8 / 64 / 6, and two shapes whose face count is a multiple of
     // the block's threads, so every warp computes the same number of faces:
     // 5 = 20x12 / 128 / 3 (512 faces), 6 = 26x14 / 128 / 3 (768 faces).
+    // For grids too small to fill the GPU, where a stage lasts as long as one
+    // thread's chain of faces, about one face per thread: 7 = 16x8 / 256 / 1
+    // (280 faces), 8 = 8x8 / 128 / 2 (144 faces).
     // The other orders use 16x16 / 128 only, 3 blocks per SM at r = 2 and 2
     // at r = 4, 5 (their wider stencils need more registers).
     if constexpr (R != 3) {  // r = 2 fits the 168-register cap of 3 blocks per SM
@@ -719,6 +722,8 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
         case 4: return launch_2d<16, 8, 64, 6, AI, P1, PREC>(a, s);
         case 5: return launch_2d<20, 12, 128, 3, AI, P1, PREC>(a, s);
         case 6: return launch_2d<26, 14, 128, 3, AI, P1, PREC>(a, s);
+        case 7: return launch_2d<16, 8, 256, 1, AI, P1, PREC>(a, s);
+        case 8: return launch_2d<8, 8, 128, 2, AI, P1, PREC>(a, s);
         default: return launch_2d<kTX, kTY, kThreads2D, 1, AI, P1, PREC>(a, s);
       }
     }
