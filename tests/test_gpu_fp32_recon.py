@@ -7,7 +7,7 @@ Runge-Kutta accumulation and the CFL reduction stay in FP64.  Its error
 against the FP64 oracle is a property of FP32 rounding, not a parity bound:
 per stage the right-hand side is within 1e-5 relative L_inf, and after full
 runs the relative L1 error of every conserved component is at most 1e-6 (the
-target of the hot-path specification).
+accuracy this mode is held to).
 """
 import numpy as np
 import pytest
