@@ -83,3 +83,18 @@ def test_entry_points_reject_bad_arguments_before_any_device_work(L):
 
 def test_version(L):
     assert "sm_103a" in weno.version()
+
+
+def test_binding_rejects_host_tensors_and_wrong_layouts():
+    """The binding refuses a state that is not a contiguous float64 CUDA
+    tensor of the descriptor's shape before it reaches the library (no CPU
+    fallback: a host tensor is an error, not a slow path)."""
+    import torch
+    d = weno.make_desc(system="euler", ndim=1, nbatch=2, nx=16)
+    assert d.shape == (2, 3, 1, 16)
+    with pytest.raises(TypeError):
+        weno.rhs(d, torch.zeros(d.shape, dtype=torch.float64))  # host memory
+    with pytest.raises(TypeError):
+        weno._state(d, torch.zeros(d.shape, dtype=torch.float32))
+    with pytest.raises(TypeError):
+        weno.step(d, torch.zeros(d.shape, dtype=torch.float64))
