@@ -66,6 +66,7 @@ def lib():
                                          ctypes.c_int, ctypes.c_int]
         for name in ("ora_alpha",):
             getattr(L, name).argtypes = [_G, _D, _D]
+        L.ora_roe_face.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D]
         L.ora_rhs.argtypes = [_G, _D, _D, _D]
         L.ora_rhs_cell.argtypes = [_G, _D, _D, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _D]
         L.ora_cfl_dt.argtypes = [_G, _D, ctypes.c_double, _D]
@@ -177,6 +178,21 @@ def coefficients_r(order):
 
 def operator_error(ncp, inv_dx, p=1.0, eps_variable=False, quad=False):
     return lib().ora_operator_error(int(ncp), int(inv_dx), float(p), int(eps_variable), int(quad))
+
+
+def roe_face(UL, UR, dir=0, gamma=1.4):
+    """Roe-averaged face state of two cells and its eigen-system (Section 4.2):
+    dict with u, v, H, c, R (columns = right eigenvectors), L (= R^-1), lam."""
+    UL = np.ascontiguousarray(UL, dtype=np.float64)
+    UR = np.ascontiguousarray(UR, dtype=np.float64)
+    nc = UL.size
+    assert UR.size == nc and nc in (3, 4)
+    out = np.zeros(40)
+    _check(lib().ora_roe_face(nc, int(dir), float(gamma), _p(UL), _p(UR), _p(out)),
+           "ora_roe_face")
+    return {"u": out[0], "v": out[1], "H": out[2], "c": out[3],
+            "R": out[4:20].reshape(4, 4)[:nc, :nc].copy(),
+            "L": out[20:36].reshape(4, 4)[:nc, :nc].copy(), "lam": out[36:36 + nc].copy()}
 
 
 def alpha(g, U):

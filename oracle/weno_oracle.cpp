@@ -559,6 +559,46 @@ double weno_flux(const ora_grid *g, const double *f) {
   return zar_flux(r, f, g->eps, g->mu0, g->p, g->ai);
 }
 
+// Roe-averaged state of two neighbouring cells and the eigen-system of the
+// flux Jacobian there (the face state of the characteristic-wise splitting,
+// Section 4.2): u, v and H averaged with the weights sqrt(rho_L), sqrt(rho_R),
+// c^2 = (gamma - 1)(H - q^2/2), R from right_eigvecs, L = R^{-1} by
+// Gauss-Jordan, and the eigenvalues lam in the order of R's columns.
+struct RoeSys {
+  double u, v, H, c;
+  double R[4][4], L[4][4], lam[4];
+};
+
+bool roe_system(int nc, int dir, double gamma, const Prim &wl, const Prim &wr, RoeSys *o) {
+  double sl = std::sqrt(wl.rho), sr = std::sqrt(wr.rho);
+  double u = (sl * wl.u + sr * wr.u) / (sl + sr);
+  double v = (sl * wl.v + sr * wr.v) / (sl + sr);
+  double H = (sl * wl.H + sr * wr.H) / (sl + sr);
+  double c2 = (gamma - 1.0) * (H - 0.5 * (u * u + v * v));
+  if (!(c2 > 0) || !finite(c2)) return false;
+  double c = std::sqrt(c2);
+  o->u = u;
+  o->v = v;
+  o->H = H;
+  o->c = c;
+  right_eigvecs(nc, dir, u, v, H, c, o->R);
+  std::memset(o->L, 0, sizeof(o->L));
+  if (!invert(nc, o->R, o->L)) return false;
+  const double un = (dir == 0) ? u : v;
+  for (int k = 0; k < 4; ++k) o->lam[k] = 0.0;
+  if (nc == 3) {
+    o->lam[0] = un - c;
+    o->lam[1] = un;
+    o->lam[2] = un + c;
+  } else {
+    o->lam[0] = un - c;
+    o->lam[1] = un;
+    o->lam[2] = un;
+    o->lam[3] = un + c;
+  }
+  return true;
+}
+
 int face_flux(const ora_grid *g, int dir, const double st[10][4], const double *alpha,
               double *Fhat) {
   const int nc = ncomp_of(g);
@@ -579,18 +619,12 @@ int face_flux(const ora_grid *g, int dir, const double st[10][4], const double *
     if (!to_prim(nc, st[j], g->gamma, &w[j])) return 2;
     euler_flux(nc, dir, st[j], w[j], F[j]);
   }
-  // Roe average of cells i (stencil index r-1) and i+1 (index r).
-  const Prim &wl = w[r - 1], &wr = w[r];
-  double sl = std::sqrt(wl.rho), sr = std::sqrt(wr.rho);
-  double u = (sl * wl.u + sr * wr.u) / (sl + sr);
-  double v = (sl * wl.v + sr * wr.v) / (sl + sr);
-  double H = (sl * wl.H + sr * wr.H) / (sl + sr);
-  double c2 = (g->gamma - 1.0) * (H - 0.5 * (u * u + v * v));
-  if (!(c2 > 0) || !finite(c2)) return 2;
-  double c = std::sqrt(c2);
-  double R[4][4], L[4][4];
-  right_eigvecs(nc, dir, u, v, H, c, R);
-  if (!invert(nc, R, L)) return 2;
+  // Roe average of cells i (stencil index r-1) and i+1 (index r), and its
+  // eigen-system.
+  RoeSys rs;
+  if (!roe_system(nc, dir, g->gamma, w[r - 1], w[r], &rs)) return 2;
+  const double(&R)[4][4] = rs.R;
+  const double(&L)[4][4] = rs.L;
   double h[4];
   for (int m = 0; m < nc; ++m) {
     double fp[10], fm[10];
@@ -778,6 +812,26 @@ double ora_operator_error(int ncp, int inv_dx, double p, int eps_variable, int u
   if (ncp < 0 || inv_dx < 3) return -1.0;
   if (use_quad) return operator_error_t<quad>(ncp, inv_dx, p, eps_variable);
   return operator_error_t<double>(ncp, inv_dx, p, eps_variable);
+}
+
+int ora_roe_face(int nc, int dir, double gamma, const double *UL, const double *UR,
+                 double *out) {
+  if ((nc != 3 && nc != 4) || dir < 0 || dir > (nc == 4 ? 1 : 0) || !(gamma > 1.0)) return 1;
+  Prim wl, wr;
+  if (!to_prim(nc, UL, gamma, &wl) || !to_prim(nc, UR, gamma, &wr)) return 2;
+  RoeSys rs;
+  if (!roe_system(nc, dir, gamma, wl, wr, &rs)) return 2;
+  out[0] = rs.u;
+  out[1] = rs.v;
+  out[2] = rs.H;
+  out[3] = rs.c;
+  for (int r = 0; r < 4; ++r)
+    for (int k = 0; k < 4; ++k) {
+      out[4 + 4 * r + k] = rs.R[r][k];
+      out[20 + 4 * r + k] = rs.L[r][k];
+    }
+  for (int k = 0; k < 4; ++k) out[36 + k] = rs.lam[k];
+  return 0;
 }
 
 // Eq. (6): alpha = max |f'(Q)|.  Reading: the maximum is taken over all cells

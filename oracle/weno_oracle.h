@@ -77,6 +77,16 @@ void ora_coefficients(double *out64);
  * quadruple precision.  p must be 1, 1.5 or 2 when use_quad = 1. */
 double ora_operator_error(int ncp, int inv_dx, double p, int eps_variable, int use_quad);
 
+/* Roe-averaged face state of two neighbouring cells UL, UR (nc = 3: 1D Euler,
+ * nc = 4: 2D Euler; dir 0 = x, 1 = y) and the eigen-system of the flux
+ * Jacobian there, the one the characteristic-wise splitting of Section 4.2
+ * projects with (the face_flux routine uses exactly this).  out[40]:
+ * u, v, H, c, R[4][4] (right eigenvectors as columns, row major), L[4][4]
+ * (= R^{-1}), lam[4] (eigenvalues in the order of R's columns); rows and
+ * columns beyond nc are 0.  Returns 0, 1 (bad argument) or 2 (nonphysical). */
+int ora_roe_face(int nc, int dir, double gamma, const double *UL, const double *UR,
+                 double *out);
+
 /* Global Lax-Friedrichs speeds of eq. (6) for a stage input U:
  * alpha[b][dir][m] = max over all cells of |lambda_m| (dir 0 = x, 1 = y,
  * m = characteristic field, 4 slots, unused ones 0).  Returns a status code. */
