@@ -74,7 +74,7 @@ typedef struct weno_desc {
   double gamma;       /* ratio of specific heats (Euler)                          */
   double cfl;         /* CFL number of the time step rule                         */
   double eps;         /* sensitivity epsilon of eq. (21); with ai = 1, >= 1e-250  */
-  double mu0;         /* mu_0 of eq. (22); with ai = 1, >= 1e-100                 */
+  double mu0;         /* mu_0 of eq. (22); with ai = 1, 16 eps mu0^2 >= 1e-300    */
   double p;           /* power parameter p of eq. (21), > 0 (the paper: 1, 3/2, 2) */
   int32_t ai;         /* 1: affine-invariant descaler mu[f] of eq. (22); 0: mu = 1 */
   int32_t precision;  /* WENO_PREC_FP64, or WENO_PREC_FP32_RECON: the indicators, */
@@ -108,12 +108,23 @@ size_t weno_workspace_bytes(const weno_desc *d);
 weno_status weno_wavespeeds(const weno_desc *d, const double *U, double *alpha, double *dt,
                             void *ws, size_t ws_bytes, void *stream);
 
+/* Tile autotuning (2D, order 6).  weno_rhs, weno_step and weno_solve choose
+ * among nine tile shapes of the 2D stage kernel (all give bitwise the same
+ * result).  The first such call on a new problem shape (nx, ny, nbatch,
+ * precision, ai, p == 1) in a process times them on the caller's data: two
+ * launches of each shape on `stream`, writing only the workspace, with CUDA
+ * events, and it synchronises the stream before it returns.  Later calls on
+ * that shape are asynchronous as stated.  The environment variable
+ * WENO_TILE2D = 0..8 forces one shape and skips the timing (use it when the
+ * first call must not synchronise, e.g. inside a stream capture). */
+
 /* Right-hand side of one Runge-Kutta stage, L(U) (eq. (5) dimension by
  * dimension: dU/dt = -(F_{i+1/2} - F_{i-1/2})/dx - (G_{j+1/2} - G_{j-1/2})/dy),
  * with the interface fluxes of WENO-ZA6 (Section 3) after global
  * Lax-Friedrichs splitting (eq. (6)), characteristic-wise on Roe-averaged
  * eigenvectors for Euler (Section 4.2), and the GLF speeds taken from U.
- * dUdt has U's layout and must not overlap U.  Asynchronous. */
+ * dUdt has U's layout and must not overlap U.  Asynchronous (but see the
+ * tile autotuning note above for the first 2D call on a new shape). */
 weno_status weno_rhs(const weno_desc *d, const double *U, double *dUdt, void *ws,
                      size_t ws_bytes, void *stream);
 
@@ -122,7 +133,8 @@ weno_status weno_rhs(const weno_desc *d, const double *U, double *dUdt, void *ws
  *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));
  *   U <- 1/3 U + 2/3 (U2 + dt L(U2)).
  * dt > 0: that step for every problem; dt <= 0: each problem's own CFL step
- * (as in weno_wavespeeds).  dt_used: NULL (asynchronous call) or a HOST
+ * (as in weno_wavespeeds).  dt_used: NULL (asynchronous call, apart from the
+ * first 2D call on a new shape, see the tile autotuning note) or a HOST
  * array of nbatch doubles that receives the steps taken; then the call
  * synchronises the stream and also reports device-side errors. */
 weno_status weno_step(const weno_desc *d, double *U, double dt, double *dt_used, void *ws,
@@ -231,6 +243,21 @@ weno_status weno_engine_retire(weno_engine *e, int slot, double *U_host, double 
 weno_status weno_engine_info(const weno_engine *e, size_t *heap_free_bytes,
                              size_t *heap_largest, int64_t *tiles_in_use);
 weno_status weno_engine_destroy(weno_engine *e);
+
+/* Measured FMA throughput of the current GPU, the peak of the stage kernels'
+ * roofline (they are bound by FP64 instruction issue; no step of the method
+ * is a dense contraction, and their HBM traffic is far below the memory
+ * roof).  The paper has no counterpart: it reports CPU times only.
+ * kind 0: FP64 FMA chains on full-mantissa values (the operands of a real
+ *         solve; on GB300 the FP64 rate depends on the operands' bits),
+ *      1: FP64 FMA chains that settle on 1.0 (a mantissa of zeros),
+ *      2: FP32 FMA chains.
+ * One launch of 8 blocks x 256 threads per SM, each thread running 8
+ * independent chains of `iters` FMAs (1 .. 2^24; 4096 takes about 20 ms in
+ * FP64 on GB300), timed with CUDA events on `stream` after a short warm-up.
+ * *flops_per_s (HOST) receives 2 x FMAs / second.  Allocates no device
+ * memory; synchronises the stream. */
+weno_status weno_fma_rate(int kind, int iters, double *flops_per_s, void *stream);
 
 /* Message describing the last error on the calling host thread ("" if none). */
 const char *weno_last_error(void);

@@ -5,6 +5,7 @@ Sections 2-4) that the CUDA library is checked against.  Only tests/, the
 smoke check in __graft_entry__ and bench.py's CPU-baseline leg may import it.
 It imports nothing from the CUDA package.
 """
+import contextlib
 import ctypes
 import os
 
@@ -12,7 +13,8 @@ import numpy as np
 
 from . import build as _build
 
-_lib = None
+_libs = {}
+_variant = None
 
 
 class OraGrid(ctypes.Structure):
@@ -45,38 +47,57 @@ _G = ctypes.POINTER(OraGrid)
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        L.ora_za6_flux.restype = ctypes.c_double
-        L.ora_za6_flux.argtypes = [_D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_int, _D]
-        L.ora_za6_flux_quad.restype = ctypes.c_double
-        L.ora_za6_flux_quad.argtypes = [_D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                        ctypes.c_int]
-        L.ora_coefficients.restype = None
-        L.ora_coefficients.argtypes = [_D]
-        L.ora_za_flux.restype = ctypes.c_double
-        L.ora_za_flux.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
-                                  ctypes.c_double, ctypes.c_int]
-        L.ora_coefficients_r.argtypes = [ctypes.c_int, _D]
-        L.ora_operator_error.restype = ctypes.c_double
-        L.ora_operator_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                         ctypes.c_int, ctypes.c_int]
-        for name in ("ora_alpha",):
-            getattr(L, name).argtypes = [_G, _D, _D]
-        L.ora_roe_face.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D]
-        L.ora_rhs.argtypes = [_G, _D, _D, _D]
-        L.ora_rhs_cell.argtypes = [_G, _D, _D, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _D]
-        L.ora_cfl_dt.argtypes = [_G, _D, ctypes.c_double, _D]
-        L.ora_ssprk3_step.argtypes = [_G, _D, _D]
-        L.ora_solve.argtypes = [_G, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_int64, _D, _I64]
-        L.ora_riemann_exact.argtypes = [ctypes.c_double] * 7 + [ctypes.c_double, ctypes.c_double,
-                                                                ctypes.c_int64, _D, _D, _D, _D, _D]
-        _lib = L
-    return _lib
+    """The oracle library of the current rounding variant (built on demand)."""
+    if _variant not in _libs:
+        _libs[_variant] = _load(_build.build(variant=_variant))
+    return _libs[_variant]
+
+
+@contextlib.contextmanager
+def rounding_variant(name):
+    """Within the block every oracle call runs the build whose final sums
+    (eq. (14), the projections on L, the back-projection on R) are taken in
+    the opposite order ("reversed"): the same arithmetic, rounded
+    differently.  None is the stock build."""
+    global _variant
+    assert name in _build.VARIANTS
+    old = _variant
+    _variant = name
+    try:
+        yield
+    finally:
+        _variant = old
+
+
+def _load(path):
+    L = ctypes.CDLL(path)
+    L.ora_za6_flux.restype = ctypes.c_double
+    L.ora_za6_flux.argtypes = [_D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_int, _D]
+    L.ora_za6_flux_quad.restype = ctypes.c_double
+    L.ora_za6_flux_quad.argtypes = [_D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int]
+    L.ora_coefficients.restype = None
+    L.ora_coefficients.argtypes = [_D]
+    L.ora_za_flux.restype = ctypes.c_double
+    L.ora_za_flux.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_int]
+    L.ora_coefficients_r.argtypes = [ctypes.c_int, _D]
+    L.ora_operator_error.restype = ctypes.c_double
+    L.ora_operator_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int]
+    for name in ("ora_alpha",):
+        getattr(L, name).argtypes = [_G, _D, _D]
+    L.ora_roe_face.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D]
+    L.ora_rhs.argtypes = [_G, _D, _D, _D]
+    L.ora_rhs_cell.argtypes = [_G, _D, _D, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _D]
+    L.ora_cfl_dt.argtypes = [_G, _D, ctypes.c_double, _D]
+    L.ora_ssprk3_step.argtypes = [_G, _D, _D]
+    L.ora_solve.argtypes = [_G, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int64, _D, _I64]
+    L.ora_riemann_exact.argtypes = [ctypes.c_double] * 7 + [ctypes.c_double, ctypes.c_double,
+                                                            ctypes.c_int64, _D, _D, _D, _D, _D]
+    return L
 
 
 def _p(a):

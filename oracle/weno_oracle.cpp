@@ -40,6 +40,17 @@ typedef long double quad;
 
 template <class R> R r_abs(R x) { return x < R(0) ? -x : x; }
 
+// Summation order of the final sums (the convex combination of eq. (14) and
+// its normaliser, the projections on L and the back-projection on R): k-th
+// term of n.  The stock build adds in index order; the build with
+// ORA_REVERSED_SUMS adds the same terms in the opposite order, a second
+// rounding of the same arithmetic that shows how much a run amplifies
+// rounding differences.
+#ifndef ORA_REVERSED_SUMS
+#define ORA_REVERSED_SUMS 0
+#endif
+inline int sum_ix(int k, int n) { return ORA_REVERSED_SUMS ? n - 1 - k : k; }
+
 // Square root: std::sqrt for double; for quad, Newton's iteration
 // y <- (y + x/y)/2 started from the double square root (quadratic convergence:
 // three steps take 53 correct bits well past 113).
@@ -183,14 +194,12 @@ void za6_flux(const R f[6], R eps, R mu0, double p, int ai, ZA6Out<R> *o) {
   for (int k = 0; k < 4; ++k) {
     R gamma_k = r_pow<R>(tau / (beta_k[k] + eps * mu * mu), p);
     alpha[k] = (R(D_NUM[k]) / R(D_DEN)) * (R(1) + gamma_k);
-    asum = asum + alpha[k];
   }
+  for (int k = 0; k < 4; ++k) asum = asum + alpha[sum_ix(k, 4)];
   // eq. (14): convex combination of the candidate fluxes.
   R fh = 0;
-  for (int k = 0; k < 4; ++k) {
-    o->omega[k] = alpha[k] / asum;
-    fh = fh + o->omega[k] * o->fk[k];
-  }
+  for (int k = 0; k < 4; ++k) o->omega[k] = alpha[k] / asum;
+  for (int k = 0; k < 4; ++k) fh = fh + o->omega[sum_ix(k, 4)] * o->fk[sum_ix(k, 4)];
   o->fhat = fh;
 }
 
@@ -356,10 +365,13 @@ double zar_flux(int r, const double *f, double eps, double mu0, double p, int ai
   for (int k = 0; k <= r; ++k) {  // eqs. (19)-(21), L = q = 1
     const double G = r_pow<double>(tau / (beta[k] + eps * mu * mu), p);
     al[k] = ((double)t.d[k] / t.d_den) * (1.0 + G);
-    asum += al[k];
   }
+  for (int k = 0; k <= r; ++k) asum += al[sum_ix(k, r + 1)];
   double fh = 0;
-  for (int k = 0; k <= r; ++k) fh += (al[k] / asum) * fk[k];  // eq. (14)
+  for (int q = 0; q <= r; ++q) {  // eq. (14)
+    const int k = sum_ix(q, r + 1);
+    fh += (al[k] / asum) * fk[k];
+  }
   return fh;
 }
 
@@ -630,7 +642,8 @@ int face_flux(const ora_grid *g, int dir, const double st[10][4], const double *
     double fp[10], fm[10];
     for (int j = 0; j < n; ++j) {
       double wc = 0, gc = 0;
-      for (int k = 0; k < nc; ++k) {
+      for (int q = 0; q < nc; ++q) {
+        const int k = sum_ix(q, nc);
         wc += L[m][k] * st[j][k];
         gc += L[m][k] * F[j][k];
       }
@@ -641,7 +654,7 @@ int face_flux(const ora_grid *g, int dir, const double st[10][4], const double *
   }
   for (int rr = 0; rr < nc; ++rr) {
     double sum = 0;
-    for (int m = 0; m < nc; ++m) sum += R[rr][m] * h[m];
+    for (int q = 0; q < nc; ++q) sum += R[rr][sum_ix(q, nc)] * h[sum_ix(q, nc)];
     Fhat[rr] = sum;
   }
   return 0;

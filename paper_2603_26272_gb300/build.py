@@ -14,7 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libweno.so")
-SOURCES = ["weno_kernels.cu", "weno_orders.cu", "weno_api.cu", "weno_noalloc.cu", "weno_engine.cu"]
+SOURCES = ["weno_kernels.cu", "weno_orders.cu", "weno_api.cu", "weno_noalloc.cu", "weno_engine.cu",
+           "weno_peak.cu"]
 HEADERS = ["weno_device.cuh", "weno_tiles.cuh", "weno_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

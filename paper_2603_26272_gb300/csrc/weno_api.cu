@@ -106,10 +106,17 @@ weno_status check_desc(const weno_desc *d) {
   if (!(d->eps > 0.0) || !std::isfinite(d->eps)) return fail(WENO_ERR_ARG, "eps must be > 0");
   if (!(d->mu0 >= 0.0) || !std::isfinite(d->mu0)) return fail(WENO_ERR_ARG, "mu0 must be >= 0");
   if (d->ai && !(d->mu0 > 0.0)) return fail(WENO_ERR_ARG, "mu0 must be > 0 with ai = 1 (eq. (22))");
-  if (d->ai && !(d->eps >= 1e-250 && d->mu0 >= 1e-100))
-    return fail(WENO_ERR_ARG, "with ai = 1 the kernels need eps >= 1e-250 and mu0 >= 1e-100 "
-                              "(their weights scale exponents, which needs eps mu^2 to stay a "
-                              "normal double)");
+  // With ai = 1 and p = 1 the kernels rescale the indicators b_k = 4 beta_k +
+  // 4 eps mu^2 by an add to their exponent fields, which is exact only for
+  // normal numbers.  A field reaches the reconstruction scaled by k >= 2, so
+  // the smallest sensitivity term is 4 eps (2 mu0)^2 = 16 eps mu0^2; it must be
+  // a normal double (1e-300 leaves eight decades above DBL_MIN), and eps >=
+  // 1e-250 keeps every b_k within 1e-254 of the largest, so the rescaled
+  // values stay normal too.
+  if (d->ai && !(d->eps >= 1e-250 && 16.0 * d->eps * d->mu0 * d->mu0 >= 1e-300))
+    return fail(WENO_ERR_ARG, "with ai = 1 the kernels need eps >= 1e-250 and 16 eps mu0^2 >= "
+                              "1e-300 (their weights scale exponents, which needs eps mu^2 to stay "
+                              "a normal double)");
   if (!(d->p > 0.0) || !std::isfinite(d->p)) return fail(WENO_ERR_ARG, "p must be > 0");
   if (d->ai != 0 && d->ai != 1) return fail(WENO_ERR_ARG, "ai must be 0 or 1");
   if (d->precision != WENO_PREC_FP64 && d->precision != WENO_PREC_FP32_RECON)

@@ -99,8 +99,9 @@ def lib():
         L.weno_last_error.argtypes = []
         L.weno_version.restype = ctypes.c_char_p
         L.weno_version.argtypes = []
+        L.weno_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, _DP, _VP]
         for name in ("weno_wavespeeds", "weno_rhs", "weno_step", "weno_solve", "weno_solve_host",
-                     "weno_sync_status", "weno_step_host"):
+                     "weno_sync_status", "weno_step_host", "weno_fma_rate"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -254,6 +255,17 @@ def step_host(desc, U_host, dt=0.0, ws=None, stream=None, device=None):
 def sync_status(desc, ws, stream=None):
     _check(lib().weno_sync_status(ctypes.byref(desc), ctypes.c_void_p(ws.data_ptr()),
                                   ctypes.c_size_t(ws.numel()), _stream(stream)))
+
+
+FMA_KINDS = {"fp64": 0, "fp64_short_mantissa": 1, "fp32": 2}
+
+
+def fma_rate(kind="fp64", iters=4096, stream=None):
+    """Measured FMA throughput of the current GPU in FLOP/s (2 per FMA):
+    'fp64' on full-mantissa operands, 'fp64_short_mantissa', or 'fp32'."""
+    out = ctypes.c_double(0.0)
+    _check(lib().weno_fma_rate(FMA_KINDS[kind], int(iters), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def version():

@@ -51,7 +51,8 @@ def test_workspace_bytes_and_argument_checks(L):
     bad = [dict(ndim=3), dict(nx=0), dict(ndim=1, ny=2), dict(gamma=1.0), dict(cfl=0.0),
            dict(eps=0.0), dict(precision="fp32_recon", ai=False), dict(system="advection", ndim=2, ny=4),
            dict(nbatch=70000), dict(x1=0.0), dict(order=5), dict(order=12), dict(order=2),
-           dict(eps=1e-260), dict(mu0=1e-120),
+           dict(eps=1e-260), dict(mu0=1e-136), dict(eps=1e-250, mu0=1e-100),
+           dict(eps=1e-200, mu0=1e-52),
            dict(order=8, precision="fp32_recon")]
     for kw in bad:
         args = dict(system="euler", ndim=2, nx=8, ny=8)
@@ -59,6 +60,12 @@ def test_workspace_bytes_and_argument_checks(L):
         d = weno.make_desc(**args)
         assert L.weno_workspace_bytes(ctypes.byref(d)) == 0, kw
         assert L.weno_last_error().decode() != ""
+
+
+def test_eps_mu0_lower_limits_are_accepted(L):
+    for eps, mu0 in ((1e-250, 3e-26), (1e-40, 3e-131), (1e-40, 1e-40)):
+        d = weno.make_desc(system="euler", ndim=2, nx=8, ny=8, eps=eps, mu0=mu0)
+        assert L.weno_workspace_bytes(ctypes.byref(d)) > 0, (eps, mu0)
 
 
 def test_every_order_of_the_family_is_accepted(L):

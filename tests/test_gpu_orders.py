@@ -2,13 +2,14 @@
 the tables of the Appendix with the weights of eqs. (16)-(22)) against the
 oracle: the right-hand side and one SSP-RK3 step at 1e-12 relative L_inf,
 full runs at 1e-10 (or 4x the oracle's own spread under rounding-level input
-noise), on 1D Euler, the scalar equations and 2D Euler, with ragged tiles,
+noise or reversed summation order), on 1D Euler, the scalar equations and 2D Euler, with ragged tiles,
 grids smaller than the stencil and both boundary kinds."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
+import rounding_spread
 from paper_2603_26272_gb300 import weno
 from paper_2603_26272_gb300 import workloads as wl
 
@@ -130,10 +131,8 @@ def test_full_runs_1d(order, name, w):
     d = desc_of(w, order)
     g = grid_of(w, d)
     U_o, t_o, n_o = oracle.solve(g, w["U"], d.cfl, w["t_final"])
-    rng = np.random.default_rng(1)
-    U_p, _, _ = oracle.solve(g, w["U"] * (1 + 1e-16 * rng.choice([-1.0, 1.0], size=w["U"].shape)),
-                             d.cfl, w["t_final"])
-    tol = max(RUN_TOL, 4.0 * rel_err(U_p, U_o))
+    tol = rounding_spread.run_bound(lambda V: oracle.solve(g, V, d.cfl, w["t_final"])[0],
+                                    w["U"], rel_err, RUN_TOL)
     Ug = torch.from_numpy(np.ascontiguousarray(w["U"])).cuda()
     t_g, n_g = weno.solve(d, Ug, w["t_final"])
     assert list(n_g) == list(n_o)
@@ -154,11 +153,9 @@ def test_full_run_2d(order):
         return U
 
     # the tenth-order run amplifies rounding-level input noise to ~2e-10 in
-    # the oracle itself; the bound is 4x that spread where it exceeds 1e-10
-    rng = np.random.default_rng(1)
-    spread = rel_err(oracle_run(U0 * (1 + 1e-16 * rng.choice([-1.0, 1.0], size=U0.shape))),
-                     oracle_run(U0))
-    tol = max(RUN_TOL, 4.0 * spread)
+    # the oracle itself; the bound is 4x the oracle's own spread where that
+    # exceeds 1e-10
+    tol = rounding_spread.run_bound(oracle_run, U0, rel_err, RUN_TOL)
     U_o = U0
     Ug = torch.from_numpy(U0).cuda()
     for k in range(30):

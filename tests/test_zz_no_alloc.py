@@ -77,3 +77,48 @@ def test_noalloc_rejects_a_batch_beyond_its_scratch():
     assert _noalloc(d, U, out) == weno.WENO_ERR_ARG
     msg = weno.lib().weno_last_error().decode()
     assert "1020" in msg and "nbatch" in msg
+
+
+def test_noalloc_reports_a_nonphysical_input_then_recovers():
+    """A negative density is reported by this call (the entry point has no
+    workspace to inspect later), with its problem and cell; the status word in
+    the shared array is cleared again by the next call, which succeeds."""
+    w = wl.riemann_batch(nbatch=3, n=200, seed=6)
+    d = weno.desc_for(w)
+    bad = w["U"].copy()
+    bad[1, 0, 0, 77] = -0.5
+    out = torch.empty(bad.shape, dtype=torch.float64, device="cuda")
+    assert _noalloc(d, torch.from_numpy(bad).cuda(), out) == weno.WENO_ERR_NONPHYSICAL
+    msg = weno.lib().weno_last_error().decode()
+    assert "problem 1" in msg and "i=77" in msg, msg
+    Ug = torch.from_numpy(w["U"]).cuda()
+    ref = weno.rhs(d, Ug).cpu().numpy()
+    assert _noalloc(d, Ug, out) == weno.WENO_OK, weno.lib().weno_last_error().decode()
+    assert _rel_err(out.cpu().numpy(), ref) <= STAGE_TOL
+
+
+def test_noalloc_takes_no_device_memory():
+    """After a first call (which may load the kernels' code), further calls
+    leave the device's free memory unchanged."""
+    d, U = _cases()[0]
+    Ug = torch.from_numpy(U).cuda()
+    out = torch.empty_like(Ug)
+    assert _noalloc(d, Ug, out) == weno.WENO_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert _noalloc(d, Ug, out) == weno.WENO_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_at_the_batch_limit():
+    """nbatch = 1020, where the status word and the speed slots fill the
+    64 KiB array exactly."""
+    w = wl.riemann_batch(nbatch=1020, n=24, seed=8)
+    d = weno.desc_for(w)
+    Ug = torch.from_numpy(np.ascontiguousarray(w["U"])).cuda()
+    ref = weno.rhs(d, Ug).cpu().numpy()
+    out = torch.full_like(Ug, float("nan"))
+    assert _noalloc(d, Ug, out) == weno.WENO_OK, weno.lib().weno_last_error().decode()
+    assert _rel_err(out.cpu().numpy(), ref) <= STAGE_TOL
