@@ -34,21 +34,23 @@ UNIT = "cell-updates/s"
 N_GRID = 2048
 SEED = 3
 
-# FP64 floating-point operations of one stage launch per cell, counted from
-# the kernel's arithmetic (fma = 2, add/mul/div/sqrt/rsqrt = 1; abs, compare
-# and integer work not counted).  Per interface (2D, one direction):
-#   Roe average and eigen-system 23, projection of 6 states and 6 fluxes 180,
-#   GLF split 96, 8 WENO-ZA6 reconstructions x 105 = 840, sums 4,
-#   back-projection 21  -> 1164.
-# Per cell: primitives and fluxes 20, flux difference 20, Runge-Kutta
-# combination 20, next-stage wavespeeds 18 -> 78.
-# Two interfaces per cell (x and y): 2 * 1164 + 78 = 2406.
-FLOPS_PER_FACE = 1164
-FLOPS_PER_CELL = 78
-FLOPS_PER_CELL_STAGE = 2 * FLOPS_PER_FACE + FLOPS_PER_CELL
-# FP64 peak: the nominal GB300 figure, 1.25 TFLOP/s (152 SMs x 2 FP64 FMA
-# lanes x 2 flop x ~2.06 GHz).
-FP64_PEAK_TFLOPS = 1.25
+# Algorithmic FP64 work of one 2D cell-update (one cell, one full SSP-RK3
+# step), counted from the steps of the method rather than from the kernel:
+# per face and direction the Roe average with R and L about 60 flops, the
+# projection of 6 states and 6 fluxes on L (6 x 2 x 4 x 4 multiply-adds) 384,
+# the GLF split 48, 8 WENO-ZA6 reconstructions of about 160 flops 1280, the
+# back-projection 32, i.e. about 1.8k; two faces per cell and three stages,
+# plus the per-cell primitives, flux difference and stage combination: about
+# 11k flops per cell-update, 3.67k per cell and stage.  (The kernel executes
+# fewer FP64 instructions than this count thanks to exact rewrites of the
+# formulas; the executed count from ncu is reported beside it when the
+# committed capture matches the current sources.)
+FLOPS_PER_CELL_UPDATE = 11000.0
+FLOPS_PER_CELL_STAGE = FLOPS_PER_CELL_UPDATE / 3.0
+# Algorithmic HBM bytes per 2D cell-update: each stage reads its input state
+# (32 B), stages 2 and 3 also read U^n, and each writes its output:
+# 32 x (2 + 3 + 3) = 256 B.
+BYTES_PER_CELL_UPDATE = 256.0
 KERNEL_SOURCES = ["paper_2603_26272_gb300/csrc/weno_tiles.cuh",
                   "paper_2603_26272_gb300/csrc/weno_kernels.cu",
                   "paper_2603_26272_gb300/csrc/weno_device.cuh"]
@@ -66,18 +68,39 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per stage launch from the committed ncu capture, if it was
-    taken on the current kernel sources."""
+def ncu_record():
+    """The committed ncu figures of the stage kernel (DRAM bytes and executed
+    FP64 operations per launch at 2048^2), if they were taken on the current
+    kernel sources; {} otherwise."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
-        return None
+        return {}
     if rec.get("kernel_hash") != kernel_hash():
-        return None
-    return rec.get("dram_bytes_per_launch_2048")
+        return {}
+    return rec
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json of this machine pool (HBM copy bandwidth), if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def fma_peaks(weno):
+    """FMA throughput of this GPU measured now (weno_fma_rate): FP64 on
+    full-mantissa operands, FP64 on short ones, FP32; best of 3 launches each,
+    in TFLOP/s."""
+    out = {}
+    for kind in ("fp64", "fp64_short_mantissa", "fp32"):
+        out[kind] = max(weno.fma_rate(kind, iters=4096 if kind != "fp32" else 65536)
+                        for _ in range(3)) / 1e12
+    return out
 
 
 class Clocks:
@@ -458,7 +481,40 @@ def main():
     stage_ms = (ms_step - alpha_ms) / 3.0
     flops = cells * FLOPS_PER_CELL_STAGE
     achieved = flops / (stage_ms / 1e3) / 1e12
-    traffic = ncu_traffic()
+    rec = ncu_record()
+    traffic = rec.get("dram_bytes_per_launch_2048")
+    clocks_peak = Clocks(gpu_id)
+    clocks_peak.start()
+    peaks = fma_peaks(weno)
+    clk_peak = clocks_peak.stop()
+    fp64_peak = max(peaks["fp64"], peaks["fp64_short_mantissa"])
+    hbm_gbs = measured_peaks().get("hbm_gbs")
+    bytes_step = cells * BYTES_PER_CELL_UPDATE
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": achieved / fp64_peak, "traffic": traffic,
+        "kernel": "k_euler2d stage launch (one SSP-RK3 stage of the 2048^2 grid)",
+        "stage_ms": stage_ms, "alpha_ms": alpha_ms, "flops_per_launch": flops,
+        "flops_per_cell_stage": FLOPS_PER_CELL_STAGE,
+        "peak_source": "measured in this run by weno_fma_rate: best FP64 FMA rate of this GPU "
+                       "(short-mantissa chains %.3f, full-mantissa %.3f TFLOP/s; FP32 %.1f)"
+                       % (peaks["fp64_short_mantissa"], peaks["fp64"], peaks["fp32"]),
+        "fp64_peak_full_mantissa": peaks["fp64"],
+        "frac_vs_full_mantissa_peak": achieved / peaks["fp64"],
+        "fp32_peak": peaks["fp32"],
+        "peak_clocks": clk_peak,
+        "hbm": {"achieved_gbs": bytes_step / (ms_step / 1e3) / 1e9, "peak_gbs": hbm_gbs,
+                "frac": (bytes_step / (ms_step / 1e3) / 1e9 / hbm_gbs) if hbm_gbs else None,
+                "bytes_per_cell_update": BYTES_PER_CELL_UPDATE,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+    }
+    fp64_ops = rec.get("fp64_flops_per_launch_2048")
+    if fp64_ops:
+        ex = fp64_ops / (stage_ms / 1e3) / 1e12
+        roofline["executed"] = {"fp64_flops_per_launch": fp64_ops, "achieved": ex,
+                                "frac": ex / fp64_peak,
+                                "source": "ncu sm__sass_thread_inst_executed_op_d{fma,add,mul}"
+                                          "_pred_on (fma = 2) of one launch, profiles/"}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -471,11 +527,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (state %.0f MB, working set %.0f MB)"
                          % (state_bytes / 1e6, 3 * state_bytes / 1e6)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "k_euler2d stage launch", "stage_ms": stage_ms,
-                     "alpha_ms": alpha_ms, "flops_per_launch": flops,
-                     "peak_source": "nominal GB300 FP64, 152 SMs x 2 FMA lanes x 2 flop x 2.06 GHz = 1.25 TFLOP/s (the FP64 pipe is not in the measured peaks)"},
+        "roofline": roofline,
         "e2e": {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
         "gpu_launches": 4 * args.steps,

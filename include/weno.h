@@ -172,6 +172,48 @@ weno_status weno_solve_host(const weno_desc *d, double *U_host, double t0, doubl
  * WENO_ERR_NONPHYSICAL with the problem, cell and stage in weno_last_error). */
 weno_status weno_sync_status(const weno_desc *d, void *ws, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Domain decomposition in y: a 2D Euler grid split into strips of rows, one
+ * per process (GPU).  d is the GLOBAL descriptor (its ny, x0..y1, bc_x, bc_y,
+ * scheme); a strip holds nrows consecutive rows, r <= nrows <= ny, r = order/2
+ * (3 for WENO-ZA6), as U = [nbatch][4][nrows][nx] with its own workspace of
+ * weno_workspace_bytes(d with ny = nrows) bytes.  One SSP-RK3 step of a strip:
+ *   weno_dd_begin(U)                 local speed maxima of U (into the slot
+ *                                    stage 1 reads) and U's first / last r rows
+ *                                    into send_lo / send_hi;
+ *   for stage = 1, 2, 3:
+ *     weno_dd_speeds(stage)          device pointer to nbatch x 8 uint64: the
+ *                                    caller replaces them in place by their
+ *                                    maximum over all strips (they are the bit
+ *                                    patterns of non-negative doubles, so an
+ *                                    integer max is the numeric max; eq. (6)
+ *                                    takes its GLF speeds over the whole grid);
+ *     exchange                       the caller sends send_lo to the strip
+ *                                    below (its halo_hi) and send_hi to the
+ *                                    strip above (its halo_lo);
+ *     weno_dd_stage(stage, halos)    the stage, reading the r rows beyond each
+ *                                    side from halo_lo / halo_hi (rows in
+ *                                    increasing order, [nbatch][4][r][nx]), or
+ *                                    from the boundary condition bc_y where a
+ *                                    halo pointer is NULL (a side of the global
+ *                                    domain); it writes its output's first /
+ *                                    last r rows into send_lo / send_hi (NULL:
+ *                                    skipped) for the next exchange.
+ * dt > 0 fixes the step; dt <= 0 takes the CFL step of eq. (6)'s global
+ * speeds, the same on every strip.  Stage 3 leaves the new state in U.  The
+ * arithmetic of every cell is that of weno_step on the whole grid, so the
+ * strips together reproduce it bit for bit.  All calls are asynchronous on
+ * `stream` (weno_dd_speeds enqueues nothing); weno_sync_status with the
+ * strip's descriptor reports device-side errors.  The paper solves on one
+ * CPU; this is how its 2D right-hand side shares out over GPUs. */
+weno_status weno_dd_begin(const weno_desc *d, int64_t nrows, const double *U, double *send_lo,
+                          double *send_hi, void *ws, size_t ws_bytes, void *stream);
+weno_status weno_dd_speeds(const weno_desc *d, int64_t nrows, int stage, void *ws,
+                           size_t ws_bytes, uint64_t **speeds);
+weno_status weno_dd_stage(const weno_desc *d, int64_t nrows, int stage, double *U, double dt,
+                          const double *halo_lo, const double *halo_hi, double *send_lo,
+                          double *send_hi, void *ws, size_t ws_bytes, void *stream);
+
 /* L(U) as weno_rhs computes it, for callers that cannot allocate device
  * memory or pass a workspace (a plug-in whose host owns all allocations, a
  * loop that must never enter the allocator, a fixed memory budget).  The

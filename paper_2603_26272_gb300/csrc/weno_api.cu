@@ -575,3 +575,106 @@ weno_status weno_sync_status(const weno_desc *d, void *ws, size_t ws_bytes, void
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Domain decomposition in y: one strip of rows of a 2D grid per process.
+// The global descriptor fixes dx, dy, the boundary conditions and the scheme;
+// the strip holds nrows rows.  Per Runge-Kutta stage the caller max-reduces
+// the strips' speed maxima (eq. (6) takes its maximum over the whole grid)
+// and exchanges r rows with the neighbouring strips; everything else is the
+// single-grid stage kernel, so a split solve gives bitwise the single-grid
+// result.
+// ---------------------------------------------------------------------------
+namespace {
+
+weno_status dd_prepare(const weno_desc *g, int64_t nrows, void *ws, size_t ws_bytes, void *stream,
+                       weno_desc *local, Ctx *c) {
+  weno_status st = check_desc(g);
+  if (st != WENO_OK) return st;
+  if (g->ndim != 2 || g->system != WENO_SYS_EULER)
+    return fail(WENO_ERR_ARG, "domain decomposition is for 2D Euler");
+  const int r = g->order == 0 ? 3 : g->order / 2;
+  if (nrows < r || nrows > g->ny)
+    return fail(WENO_ERR_ARG, "nrows must be at least r = " + std::to_string(r) +
+                                  " (the rows a neighbour needs) and at most ny");
+  *local = *g;
+  local->ny = nrows;
+  return prepare(local, ws, ws_bytes, stream, false, c);
+}
+
+int order_r_of(const weno_desc *d) { return d->order == 0 ? 3 : d->order / 2; }
+
+}  // namespace
+
+extern "C" {
+
+weno_status weno_dd_begin(const weno_desc *d, int64_t nrows, const double *U, double *send_lo,
+                          double *send_hi, void *ws, size_t ws_bytes, void *stream) {
+  weno_desc local;
+  Ctx c;
+  weno_status st = dd_prepare(d, nrows, ws, ws_bytes, stream, &local, &c);
+  if (st != WENO_OK) return st;
+  if (!U) return fail(WENO_ERR_ARG, "NULL state");
+  if ((st = reset_control(c, 0.0)) != WENO_OK) return st;
+  AlphaArgs a = alpha_args(c, U, c.slot(0));
+  a.dy = (d->y1 - d->y0) / (double)d->ny;
+  cudaError_t e = weno::launch_alpha(a, c.s);
+  if (e != cudaSuccess) return cuda_fail(e, "alpha launch");
+  const int r = order_r_of(d);
+  if (send_lo) e = weno::launch_pack_rows(U, d->nbatch, 4, nrows, d->nx, 0, r, send_lo, c.s);
+  if (e == cudaSuccess && send_hi)
+    e = weno::launch_pack_rows(U, d->nbatch, 4, nrows, d->nx, nrows - r, r, send_hi, c.s);
+  if (e != cudaSuccess) return cuda_fail(e, "row pack launch");
+  return WENO_OK;
+}
+
+weno_status weno_dd_speeds(const weno_desc *d, int64_t nrows, int stage, void *ws, size_t ws_bytes,
+                           uint64_t **speeds) {
+  weno_desc local;
+  Ctx c;
+  weno_status st = dd_prepare(d, nrows, ws, ws_bytes, nullptr, &local, &c);
+  if (st != WENO_OK) return st;
+  if (stage < 1 || stage > 3) return fail(WENO_ERR_ARG, "stage must be 1, 2 or 3");
+  if (!speeds) return fail(WENO_ERR_ARG, "NULL output");
+  *speeds = (uint64_t *)c.slot(stage - 1);
+  return WENO_OK;
+}
+
+weno_status weno_dd_stage(const weno_desc *d, int64_t nrows, int stage, double *U, double dt,
+                          const double *halo_lo, const double *halo_hi, double *send_lo,
+                          double *send_hi, void *ws, size_t ws_bytes, void *stream) {
+  weno_desc local;
+  Ctx c;
+  weno_status st = dd_prepare(d, nrows, ws, ws_bytes, stream, &local, &c);
+  if (st != WENO_OK) return st;
+  if (stage < 1 || stage > 3) return fail(WENO_ERR_ARG, "stage must be 1, 2 or 3");
+  if (!U) return fail(WENO_ERR_ARG, "NULL state");
+  if (!std::isfinite(dt)) return fail(WENO_ERR_ARG, "dt must be finite");
+  StageArgs a = stage_args(c);
+  a.dy = (d->y1 - d->y0) / (double)d->ny;
+  const int forced = tile_override();
+  a.tile_variant = forced >= 0 ? forced : 3;  // every variant gives the same bits
+  a.mode = 0;
+  a.stage = stage;
+  a.dt_fixed = dt > 0.0 ? dt : 0.0;
+  a.t_final = INFINITY;
+  if (stage == 1) {
+    a.Uin = U; a.Un = nullptr; a.Uout = c.u1(); a.a_n = 0.0; a.a_s = 1.0;
+  } else if (stage == 2) {
+    a.Uin = c.u1(); a.Un = U; a.Uout = c.u2(); a.a_n = 0.75; a.a_s = 0.25;
+  } else {
+    a.Uin = c.u2(); a.Un = U; a.Uout = U; a.a_n = 1.0 / 3.0; a.a_s = 2.0 / 3.0;
+  }
+  a.alpha_in = c.slot(stage - 1);
+  a.alpha_out = stage < 3 ? c.slot(stage) : nullptr;
+  a.alpha_zero = c.slot(stage + 1);
+  a.halo_lo = halo_lo;
+  a.halo_hi = halo_hi;
+  a.send_lo = send_lo;
+  a.send_hi = send_hi;
+  cudaError_t e = weno::launch_stage(a, c.s);
+  if (e != cudaSuccess) return cuda_fail(e, "stage launch");
+  return WENO_OK;
+}
+
+}  // extern "C"

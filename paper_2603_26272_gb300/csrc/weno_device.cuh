@@ -87,6 +87,29 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL);
 }
 
+// 1/x for a positive normal x (the divisions of the stage kernels: the Roe
+// weights, the weight denominators, 1/rho), by Newton-Raphson.  With
+// x = m 2^E, m in [1, 2), the seed is the FP32 approximate reciprocal of m
+// (rcp.approx.ftz.f32 on the special-function unit, within about 2^-22
+// of 1/m after the rounding of m to FP32) scaled by 2^-E on the integer pipe;
+// one cubic Newton-Raphson step, r <- r + r (e + e^2) with e = 1 - x r,
+// leaves a relative error of about e^3 < 2^-66, so the result is 1/x to
+// within the FP64 rounding of its three fused multiply-adds (about 1 ulp).
+// Three FP64 operations instead of the ~8 pipe slots of an IEEE division.
+// (Inputs outside the positive normal range -- a nonphysical state, which
+// the kernels report separately -- give a meaningless but finite value.)
+__device__ __forceinline__ double rcp_pos(double x) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7FF;
+  const double m = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, __double2loint(x));
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__double2float_rn(m)));
+  double r = (double)rf;
+  r = __hiloint2double(__double2hiint(r) - ((ex - 1023) << 20), __double2loint(r));
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
 // ---------------------------------------------------------------------------
 // WENO-ZA6 numerical flux at x_{i+1/2} from v0..v5 = f_{i-2}..f_{i+3}
 // (positive flux; the negative flux is this routine on the mirrored stencil).
@@ -102,19 +125,31 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 //   eps mu^2))^p (eq. (21)), alpha_k = d_k (1 + Gamma_k) (eq. (20), L = q = 1),
 //   f = sum alpha_k f^k / sum alpha_k (eqs. (14), (19)), d = (1, 9, 9, 1)/20.
 //
-// The routine returns the parts v2, num = sum a_k r_k and den = sum a_k with
-// a_k proportional to alpha_k, so f = v2 + num / (6 den); pair_flux below
-// adds the positive and negative fluxes of a field with one division.
+// The routine takes the five differences d_j (it never needs the values
+// themselves) and returns num = sum a_k r_k and den = sum a_k with a_k
+// proportional to alpha_k, so f = v2 + num / (6 den); field_flux below forms
+// the differences of a field's positive and mirrored negative fluxes and
+// adds the two reconstructions with one reciprocal.
 // b_k = 4 beta_k + 4 eps mu^2 is formed as 13/3 s_k^2 + (t_k^2 + e), and
 // b_3 = mean of b_0, b_1, b_2, b_d (the same number as 4 beta_3 + e).
 // (The bound on the spread of the b_k with Ai: each 4 beta_k is at most ~1e4
 // mu^2 and e = 4e-40 mu^2, so min b / max b > ~1e-44.)
 //
-// For p = 1 the four divisions tau/b_k are removed: a_k = (b_k + 4 tau)
-// prod_{j != k} b_j (times d_k / d_0).  Before the products, the b_k and
-// 4 tau are multiplied by the power of two that brings their maximum into
-// [1, 2) (built from the exponent bits), so the products -- and the product
-// of two denominators in pair_flux -- can neither overflow nor underflow.
+// For p = 1 the four divisions tau/b_k are removed: a_k is proportional to
+// (b_k + 4 tau) prod_{j != k} b_j = P + 4 tau Q_k with P = prod b_j and
+// Q_k = prod_{j != k} b_j (one fused multiply-add each).  Before the
+// products, the b_k and 4 tau are multiplied by the power of two that brings
+// their maximum into [1, 2) (built from the exponent bits), and the scaled
+// b_k are floored at 2^-166, so the products -- and the product of two
+// denominators in pair_flux, at least 2^-996 -- can neither overflow nor
+// underflow.  The floor acts only on a substencil flatter than 2^-166 of the
+// largest indicator (never with Ai and eps >= 1e-40, where the spread is
+// below 2^-142; possible with a tiny eps or without Ai on large data).  Such
+// substencils' candidates differ from one another by less than 2^-80 of the
+// stencil's variation, and 4 tau, when not 0, is above 2^-104 of the largest
+// indicator (it is the square of a difference of the d_j, which is 0 or at
+// least an ulp of them), so their weights keep dominating the others and
+// the flux moves by less than that 2^-80.
 //
 // mu is formed in FP32 from the FP64 differences: it enters only through
 // eps mu^2 with eps = 1e-40, which matters only for a substencil whose
@@ -124,15 +159,12 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 // FP64; the rescale below relies on mu being right to within that 1e-7.
 // ---------------------------------------------------------------------------
 struct ZA6Part {
-  double v2, num, den;  // f = v2 + num / (6 den)
+  double num, den;  // f = v2 + num / (6 den)
 };
 
-
-
 template <bool AI, bool P1>
-__device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v3, double v4,
-                                       double v5, const ReconParams &P) {
-  const double d0 = v1 - v0, d1 = v2 - v1, d2 = v3 - v2, d3 = v4 - v3, d4 = v5 - v4;
+__device__ __forceinline__ ZA6Part za6d(double d0, double d1, double d2, double d3, double d4,
+                                        const ReconParams &P) {
   const double s0 = d1 - d0, s1 = d2 - d1, s2 = d3 - d2, s3 = d4 - d3;
   const double t0 = fma(3.0, d1, -d0);
   const double t1 = d1 + d2;
@@ -199,11 +231,16 @@ __device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v
       b3 = bsum * (0.25 * sc);
     }
     const double T = T0 * __longlong_as_double((2048LL - ex) << 52);  // 4 tau, scaled
+    const long long floor_bits = (1023LL - 166) << 52;  // 2^-166 (b_3 >= max / 4 needs none)
+    b0 = __longlong_as_double(max(__double_as_longlong(b0), floor_bits));
+    b1 = __longlong_as_double(max(__double_as_longlong(b1), floor_bits));
+    b2 = __longlong_as_double(max(__double_as_longlong(b2), floor_bits));
     const double p01 = b0 * b1, p23 = b2 * b3;
-    a0 = (b0 + T) * (b1 * p23);
-    a1 = (b1 + T) * (b0 * p23);
-    a2 = (b2 + T) * (b3 * p01);
-    a3 = (b3 + T) * (b2 * p01);
+    const double Pall = p01 * p23;
+    a0 = fma(T, b1 * p23, Pall);
+    a1 = fma(T, b0 * p23, Pall);
+    a2 = fma(T, b3 * p01, Pall);
+    a3 = fma(T, b2 * p01, Pall);
   } else {
     const double T = 4.0 * T0;
     const double b3 = 0.25 * bsum;
@@ -213,17 +250,40 @@ __device__ __forceinline__ ZA6Part za6(double v0, double v1, double v2, double v
     a3 = 1.0 + pow(T / b3, P.p);
   }
   ZA6Part o;  // the linear weights 1 : 9 : 9 : 1 applied here
-  o.v2 = v2;
   o.num = fma(9.0, fma(a1, r1, a2 * r2), fma(a0, r0, a3 * r3));
   o.den = fma(9.0, a1 + a2, a0 + a3);
   return o;
 }
 
 // f^+_{i+1/2} + f^-_{i+1/2} of one field from its two reconstructions, with
-// one division: v2+ + v2- + (n+ d- + n- d+) / (6 d+ d-).
-__device__ __forceinline__ double pair_flux(const ZA6Part &p, const ZA6Part &m) {
-  const double q = fma(p.num, m.den, m.num * p.den) / (p.den * m.den);
-  return fma(q, 1.0 / 6.0, p.v2 + m.v2);
+// one reciprocal: base + (n+ d- + n- d+) / (6 d+ d-), where base = v2+ + v2-
+// is the sum of the two stencils' centre values.
+__device__ __forceinline__ double pair_flux(double base, const ZA6Part &p, const ZA6Part &m) {
+  const double q = fma(p.num, m.den, m.num * p.den) * rcp_pos(p.den * m.den);
+  return fma(q, 1.0 / 6.0, base);
+}
+
+// One characteristic field of one face (FP64): w[j], g[j] are the projected
+// states and fluxes of the six stencil cells i-2 .. i+3 and A the field's GLF
+// speed.  The split of eq. (6) (kernel scaling: without the 1/2) is applied
+// to the differences: f+ = g + A w has differences dg + A dw, and the
+// mirrored f- = g - A w, read from i+3 down to i-2, has differences
+// A dw - dg in reverse order; the two centre values add up to
+// (g_i + g_{i+1}) - A (w_{i+1} - w_i).  Returns h = f^+ + f^- at i+1/2.
+template <bool AI, bool P1>
+__device__ __forceinline__ double field_flux(const double (&w)[6], const double (&g)[6], double A,
+                                             const ReconParams &P) {
+  double dp[5], dm[5], dw2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const double dw = w[j + 1] - w[j], dg = g[j + 1] - g[j];
+    dp[j] = fma(A, dw, dg);
+    dm[4 - j] = fma(A, dw, -dg);
+    if (j == 2) dw2 = dw;
+  }
+  const double base = fma(-A, dw2, g[2] + g[3]);
+  return pair_flux(base, za6d<AI, P1>(dp[0], dp[1], dp[2], dp[3], dp[4], P),
+                   za6d<AI, P1>(dm[0], dm[1], dm[2], dm[3], dm[4], P));
 }
 
 // ---------------------------------------------------------------------------
@@ -434,6 +494,14 @@ __device__ __forceinline__ RPart za_r(const double (&v)[2 * R], const ReconParam
       for (int k = 0; k <= R; ++k) b[k] *= sc;
     }
     const double T = T0 * __longlong_as_double((2046LL - ex) << 52);
+    // floor of the scaled indicators, as in za6d: 2^(-1000 / 2R) up to R = 4,
+    // where the product of two denominators holds 2R of them, 2^-200 at R = 5
+    // (no product of denominators; a Q_k holds 5)
+    constexpr long long kFloorExp = (R == 5) ? 200 : 1000 / (2 * R);
+    const long long floor_bits = (1023LL - kFloorExp) << 52;
+#pragma unroll
+    for (int k = 0; k <= R; ++k)
+      b[k] = __longlong_as_double(max(__double_as_longlong(b[k]), floor_bits));
     // a_k = (b_k + T) prod_{j != k} b_j from prefix and suffix products
     double pre[R + 1], suf[R + 1];
     pre[0] = 1.0;
@@ -442,10 +510,11 @@ __device__ __forceinline__ RPart za_r(const double (&v)[2 * R], const ReconParam
     for (int k = 1; k <= R; ++k) pre[k] = (k == 1) ? b[0] : pre[k - 1] * b[k - 1];
 #pragma unroll
     for (int k = R - 1; k >= 0; --k) suf[k] = (k == R - 1) ? b[R] : suf[k + 1] * b[k + 1];
+    const double Pall = pre[R] * b[R];  // prod of all b_j
 #pragma unroll
     for (int k = 0; k <= R; ++k) {
       const double pk = (k == 0) ? suf[0] : (k == R ? pre[R] : pre[k] * suf[k]);
-      a[k] = (b[k] + T) * pk;
+      a[k] = fma(T, pk, Pall);  // (b_k + T) prod_{j != k} b_j
     }
   } else {
     const double T = T0;
@@ -474,10 +543,10 @@ __device__ __forceinline__ RPart za_r(const double (&v)[2 * R], const ReconParam
 template <int R>
 __device__ __forceinline__ double pair_flux_r(const RPart &p, const RPart &m) {
   if (R <= 4) {
-    const double q = fma(p.num, m.den, m.num * p.den) / (p.den * m.den);
+    const double q = fma(p.num, m.den, m.num * p.den) * rcp_pos(p.den * m.den);
     return (p.vc + m.vc) + q;
   }
-  return (p.vc + p.num / p.den) + (m.vc + m.num / m.den);
+  return (p.vc + p.num * rcp_pos(p.den)) + (m.vc + m.num * rcp_pos(m.den));
 }
 
 // ---------------------------------------------------------------------------
@@ -603,18 +672,19 @@ __device__ __forceinline__ double field_flux_f32(const double (&w)[6], const dou
 // the back-projection divides again.
 // ---------------------------------------------------------------------------
 struct FaceState {
-  double un, ut, H, c, ic, b1, b2, hq2;  // Roe-averaged face state
+  double un, ut, H, c, ic, b1, b2, hq2, q2;  // Roe-averaged face state
 };
 
 __device__ __forceinline__ bool roe_face(double sl, double unl, double utl, double Hl, double sr,
                                          double unr, double utr, double Hr, double gm1,
                                          FaceState &f) {
-  const double inv = 1.0 / (sl + sr);
+  const double inv = rcp_pos(sl + sr);
   const double wl = sl * inv, wr = sr * inv;
   f.un = fma(wl, unl, wr * unr);
   f.ut = fma(wl, utl, wr * utr);
   f.H = fma(wl, Hl, wr * Hr);
   const double q2 = fma(f.un, f.un, f.ut * f.ut);
+  f.q2 = q2;
   f.hq2 = 0.5 * q2;
   const double c2 = gm1 * (f.H - f.hq2);
   if (!pos_finite(c2)) return false;
@@ -655,18 +725,21 @@ __device__ __forceinline__ void project_flux4(const FaceState &f, double unj, do
   g4 = fma(unj, w4, pz + pc);
 }
 
-// Physical flux from h = (h1, h2, h3, h4) reconstructed in the scaled
-// characteristic fields: e = (h1/4, h2/2, h3/2, h4/4) then F = R e.
+// Four times the physical flux from h = (h1, h2, h3, h4) reconstructed in
+// the scaled characteristic fields: with e = (h1/4, h2/2, h3/2, h4/4),
+// 4 F = 4 R e = R (h1, 2 h2, 2 h3, h4); the 1/4 is applied with 1/dx in the
+// flux difference, so no multiplication by it is spent here.
 __device__ __forceinline__ void backproject4(const FaceState &f, double h1, double h2, double h3,
                                              double h4, double &F0, double &F1, double &F2,
                                              double &F3) {
-  const double e1 = 0.25 * h1, e2 = 0.5 * h2, e3 = 0.5 * h3, e4 = 0.25 * h4;
-  const double S = (e1 + e4) + e2;
-  const double D = e4 - e1;
+  const double h14 = h1 + h4;
+  const double S = fma(2.0, h2, h14);  // 4 (e1 + e2 + e4)
+  const double D = h4 - h1;            // 4 (e4 - e1)
+  const double h3x2 = h3 + h3;         // 4 e3
   F0 = S;
   F1 = fma(f.un, S, f.c * D);
-  F2 = fma(f.ut, S, e3);
-  F3 = fma(f.H, e1 + e4, fma(f.un * f.c, D, fma(f.hq2, e2, f.ut * e3)));
+  F2 = fma(f.ut, S, h3x2);
+  F3 = fma(f.H, h14, fma(f.un * f.c, D, fma(f.q2, h2, f.ut * h3x2)));
 }
 
 // 1D Euler (rho, m, E): R = [(1, u-c, H-uc), (1, u, u^2/2), (1, u+c, H+uc)],
@@ -694,14 +767,15 @@ __device__ __forceinline__ double project3_field(const FaceState &f, int q, doub
   return fma(q == 0 ? t : -t, f.ic, z);
 }
 
+// Four times the 1D physical flux, 4 F = R (h1, 2 h2, h3), as backproject4.
 __device__ __forceinline__ void backproject3(const FaceState &f, double h1, double h2, double h3,
                                              double &F0, double &F1, double &F2) {
-  const double e1 = 0.25 * h1, e2 = 0.5 * h2, e3 = 0.25 * h3;
-  const double S = (e1 + e3) + e2;
-  const double D = e3 - e1;
+  const double h13 = h1 + h3;
+  const double S = fma(2.0, h2, h13);
+  const double D = h3 - h1;
   F0 = S;
   F1 = fma(f.un, S, f.c * D);
-  F2 = fma(f.H, e1 + e3, fma(f.un * f.c, D, f.hq2 * e2));
+  F2 = fma(f.H, h13, fma(f.un * f.c, D, f.q2 * h2));
 }
 
 }  // namespace weno

@@ -48,6 +48,12 @@ struct StageArgs {
   double *t, *tnext, *dt;              // [nbatch]
   long long *steps;                    // [nbatch]
   DevStatus *status;
+  // 2D strip of a domain split in y (NULL when unused): the r ghost rows
+  // below row 0 / above row ny-1 come from halo_lo / halo_hi ([nbatch][4][r][nx],
+  // rows in increasing j) instead of the boundary condition, and the stage
+  // output's first / last r rows are copied into send_lo / send_hi (same layout).
+  const double *halo_lo, *halo_hi;
+  double *send_lo, *send_hi;
 };
 
 // Wavespeed reduction of U into alpha_out (which must be zero), optional dt.
@@ -107,6 +113,10 @@ cudaError_t launch_stage_orders(const StageArgs &a, cudaStream_t s);
 cudaError_t launch_alpha_export(const AlphaArgs &a, const unsigned long long *bits, double *alpha,
                                 double *dt, cudaStream_t s);
 cudaError_t launch_fill(double *p, long long n, double v, cudaStream_t s);
+// Rows [j0, j0 + nr) of every problem and component of a 2D state
+// [nbatch][nc][ny][nx] into a contiguous [nbatch][nc][nr][nx] buffer.
+cudaError_t launch_pack_rows(const double *U, long long nbatch, int nc, long long ny, long long nx,
+                             long long j0, long long nr, double *out, cudaStream_t s);
 
 // Maximiser of the Buckley-Leverett speed f' on [0, 1].
 double bl_speed_argmax();

@@ -85,6 +85,16 @@ __global__ void k_alpha_export(const AlphaArgs a, const unsigned long long *bits
   if (dt) dt[b] = cfl_dt(a.system, a.ndim, a.nc, a.cfl, a.dx, a.dy, a.adv_speed, al, a.ustar);
 }
 
+__global__ void k_pack_rows(const double *U, long long nplanes, long long ny, long long nx,
+                            long long j0, long long nr, double *out) {
+  const long long per = nr * nx, n = nplanes * per;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long pl = k / per, rem = k - pl * per;
+    out[k] = U[pl * ny * nx + j0 * nx + rem];
+  }
+}
+
 __global__ void k_fill(double *p, long long n, double v) {
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x)
@@ -132,6 +142,8 @@ __device__ __forceinline__ StageArgs slot_stage_args(const SlotDev &S, int stage
   a.stage = stage;
   a.dt_fixed = 0.0;
   a.t_final = S.t_final;
+  a.halo_lo = a.halo_hi = nullptr;
+  a.send_lo = a.send_hi = nullptr;
   a.t = S.clock;
   a.tnext = S.clock + 1;
   a.dt = S.clock + 2;
@@ -229,6 +241,16 @@ cudaError_t launch_alpha_export(const AlphaArgs &a, const unsigned long long *bi
                                 double *dt, cudaStream_t s) {
   const unsigned nb = (unsigned)((a.nbatch + 127) / 128);
   k_alpha_export<<<nb, 128, 0, s>>>(a, bits, alpha, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_rows(const double *U, long long nbatch, int nc, long long ny, long long nx,
+                             long long j0, long long nr, double *out, cudaStream_t s) {
+  const long long n = nbatch * nc * nr * nx;
+  if (n <= 0) return cudaSuccess;
+  long long nb = (n + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  k_pack_rows<<<(unsigned)nb, 256, 0, s>>>(U, nbatch * nc, ny, nx, j0, nr, out);
   return cudaGetLastError();
 }
 

@@ -218,9 +218,22 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
     const bool xb = (r >= R) && (r < R + TY), yb = (c >= R) && (c < R + TX);
     if (!(xb || yb)) continue;
     const long long gi = ghost(i0 - R + c, a.nx, a.bc_x);
-    const long long gj = ghost(j0 - R + r, a.ny, a.bc_y);
-    const long long o = gj * a.nx + gi;
-    const double rho = Ub[o], mx = Ub[plane + o], my = Ub[2 * plane + o], E = Ub[3 * plane + o];
+    const long long jj = j0 - R + r;
+    const double *src = Ub;
+    long long o, pst = plane, gj = jj;
+    if (jj < 0 && a.halo_lo) {  // a neighbour's rows below this strip
+      src = a.halo_lo + b * 4 * (R * a.nx);
+      o = (jj + R) * a.nx + gi;
+      pst = R * a.nx;
+    } else if (jj >= a.ny && a.halo_hi) {  // above it (rows beyond ny+R-1 only
+      src = a.halo_hi + b * 4 * (R * a.nx);  // fill a partial tile: any halo row)
+      o = min(jj - a.ny, (long long)(R - 1)) * a.nx + gi;
+      pst = R * a.nx;
+    } else {
+      gj = ghost(jj, a.ny, a.bc_y);
+      o = gj * a.nx + gi;
+    }
+    const double rho = src[o], mx = src[pst + o], my = src[2 * pst + o], E = src[3 * pst + o];
     const double rs = rsqrt(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
     const double ir = rs * rs;
     const double u = mx * ir, v = my * ir;
@@ -288,6 +301,21 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
       h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
       h4 = field_flux_f32<P1>(W[3], G[3], A4, r32);
+    } else if constexpr (R == 3) {
+      // WENO-ZA6: the projections, then per field the split differences
+      double W[4][6], G[4][6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int k = base + j * stride;
+        project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], W[0][j],
+                 W[1][j], W[2][j], W[3][j]);
+        project_flux4(fs, pl[pun * REG + k], pl[8 * REG + k], W[0][j], W[1][j], W[2][j],
+                      W[3][j], G[0][j], G[1][j], G[2][j], G[3][j]);
+      }
+      h1 = field_flux<AI, P1>(W[0], G[0], A1, rp4);
+      h2 = field_flux<AI, P1>(W[1], G[1], A2, rp2);
+      h3 = field_flux<AI, P1>(W[2], G[2], A3, rp2);
+      h4 = field_flux<AI, P1>(W[3], G[3], A4, rp4);
     } else {
       // f^+ in stencil order, f^- mirrored (its upwind side is on the right).
       constexpr int N = 2 * R;
@@ -307,21 +335,10 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
         p4[j] = fma(A4, w4, g4);
         m4[N - 1 - j] = fma(-A4, w4, g4);
       }
-      if constexpr (R == 3) {
-        h1 = pair_flux(za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4),
-                       za6<AI, P1>(m1[0], m1[1], m1[2], m1[3], m1[4], m1[5], rp4));
-        h2 = pair_flux(za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2),
-                       za6<AI, P1>(m2[0], m2[1], m2[2], m2[3], m2[4], m2[5], rp2));
-        h3 = pair_flux(za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp2),
-                       za6<AI, P1>(m3[0], m3[1], m3[2], m3[3], m3[4], m3[5], rp2));
-        h4 = pair_flux(za6<AI, P1>(p4[0], p4[1], p4[2], p4[3], p4[4], p4[5], rp4),
-                       za6<AI, P1>(m4[0], m4[1], m4[2], m4[3], m4[4], m4[5], rp4));
-      } else {
-        h1 = pair_flux_r<R>(za_r<R, AI, P1>(p1, rp4), za_r<R, AI, P1>(m1, rp4));
-        h2 = pair_flux_r<R>(za_r<R, AI, P1>(p2, rp2), za_r<R, AI, P1>(m2, rp2));
-        h3 = pair_flux_r<R>(za_r<R, AI, P1>(p3, rp2), za_r<R, AI, P1>(m3, rp2));
-        h4 = pair_flux_r<R>(za_r<R, AI, P1>(p4, rp4), za_r<R, AI, P1>(m4, rp4));
-      }
+      h1 = pair_flux_r<R>(za_r<R, AI, P1>(p1, rp4), za_r<R, AI, P1>(m1, rp4));
+      h2 = pair_flux_r<R>(za_r<R, AI, P1>(p2, rp2), za_r<R, AI, P1>(m2, rp2));
+      h3 = pair_flux_r<R>(za_r<R, AI, P1>(p3, rp2), za_r<R, AI, P1>(m3, rp2));
+      h4 = pair_flux_r<R>(za_r<R, AI, P1>(p4, rp4), za_r<R, AI, P1>(m4, rp4));
     }
     double F0, F1, F2, F3;
     backproject4(fs, h1, h2, h3, h4, F0, F1, F2, F3);
@@ -334,7 +351,8 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
   __syncthreads();
 
   // Phase 3: conservative difference, RK combination, next-stage speeds.
-  const double idx = 1.0 / a.dx, idy = 1.0 / a.dy;
+  // The faces hold 4 F (backproject4), so 1/4 goes with 1/dx, 1/dy.
+  const double idx = 0.25 / a.dx, idy = 0.25 / a.dy;
   unsigned long long mx6[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
   const bool want_alpha = (a.mode == 0) && (a.alpha_out != nullptr);
   for (int k = tid; k < TX * TY; k += blockDim.x) {
@@ -359,8 +377,14 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       }
       a.Uout[o + q * plane] = uo[q];
     }
+    if (a.send_lo && gj < R)  // edge rows of the output for the strips below / above
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a.send_lo[((b * 4 + q) * R + gj) * a.nx + gi] = uo[q];
+    if (a.send_hi && gj >= a.ny - R)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a.send_hi[((b * 4 + q) * R + (gj - (a.ny - R))) * a.nx + gi] = uo[q];
     if (want_alpha) {
-      const double ir = 1.0 / uo[0];
+      const double ir = rcp_pos(uo[0]);
       const double u = uo[1] * ir, v = uo[2] * ir;
       const double p = gm1 * (uo[3] - 0.5 * fma(uo[1], u, uo[2] * v));
       if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
@@ -479,17 +503,14 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
         h = field_flux_f32<P1>(W, G, A, make_r32(a));
       } else {
         const ReconParams rp = make_rp(a, q == 1 ? 2.0 : 4.0);
-        double pp[6], mm[6];  // f^- mirrored
+        double W[6], G[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
           const int k = f + j;
-          const double w = project3_field(fs, q, pl[0][k], pl[1][k], pl[2][k]);
-          const double g = project3_field(fs, q, pl[6][k], pl[7][k], pl[8][k]);
-          pp[j] = fma(A, w, g);
-          mm[5 - j] = fma(-A, w, g);
+          W[j] = project3_field(fs, q, pl[0][k], pl[1][k], pl[2][k]);
+          G[j] = project3_field(fs, q, pl[6][k], pl[7][k], pl[8][k]);
         }
-        h = pair_flux(za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp),
-                      za6<AI, P1>(mm[0], mm[1], mm[2], mm[3], mm[4], mm[5], rp));
+        h = field_flux<AI, P1>(W, G, A, rp);
       }
       hb[3 * f + q] = h;
     }
@@ -504,25 +525,30 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
   } else if constexpr (LANES == 2) {
     // the positive (even lane) and the mirrored negative flux (odd lane) of a
     // scalar face; the partial sums meet by a lane shuffle
+    // (the differences and the centre sum as field_flux forms them)
     const int f = tid >> 1, sgn = tid & 1;
     const bool act = (f <= T) && (i0 + f - 1 < nx);
-    ZA6Part part = {0.0, 0.0, 1.0};
+    ZA6Part part = {0.0, 1.0};
+    double base = 0.0;
     if (act) {
       const double A = scalar_alpha_of(a.system, a.adv_speed, a.ustar, a.alpha_in + b * 8);
-      const double As = sgn ? -A : A;
       const ReconParams rp = make_rp(a, 2.0);
-      double v[6];
+      double dd[5], dw2 = 0.0;
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int k = sgn ? f + 5 - j : f + j;
-        v[j] = fma(As, pl[0][k], pl[1][k]);
+      for (int j = 0; j < 5; ++j) {
+        const double dw = pl[0][f + j + 1] - pl[0][f + j], dg = pl[1][f + j + 1] - pl[1][f + j];
+        if (sgn)
+          dd[4 - j] = fma(A, dw, -dg);
+        else
+          dd[j] = fma(A, dw, dg);
+        if (j == 2) dw2 = dw;
       }
-      part = za6<AI, P1>(v[0], v[1], v[2], v[3], v[4], v[5], rp);
+      base = fma(-A, dw2, pl[1][f + 2] + pl[1][f + 3]);
+      part = za6d<AI, P1>(dd[0], dd[1], dd[2], dd[3], dd[4], rp);
     }
-    const ZA6Part other = {__shfl_xor_sync(0xffffffffu, part.v2, 1),
-                           __shfl_xor_sync(0xffffffffu, part.num, 1),
+    const ZA6Part other = {__shfl_xor_sync(0xffffffffu, part.num, 1),
                            __shfl_xor_sync(0xffffffffu, part.den, 1)};
-    if (act && sgn == 0) fl[f][0] = 0.5 * pair_flux(part, other);
+    if (act && sgn == 0) fl[f][0] = pair_flux(base, part, other);
   } else {
     const int f = tid;  // face between cells i0+f-1 and i0+f; stencil f..f+2R-1
     if (f <= T && i0 + f - 1 < nx) {
@@ -537,6 +563,14 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             g[j] = pl[1][f + j];
           }
           h = field_flux_f32<P1>(w, g, A, make_r32(a));
+        } else if constexpr (R == 3) {
+          double w[6], g[6];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            w[j] = pl[0][f + j];
+            g[j] = pl[1][f + j];
+          }
+          h = field_flux<AI, P1>(w, g, A, make_rp(a, 2.0));
         } else {
           const ReconParams rp = make_rp(a, 2.0);
           double pp[N], mm[N];  // f^+ in stencil order, f^- mirrored
@@ -546,13 +580,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             pp[j] = fma(A, v, fv);
             mm[N - 1 - j] = fma(-A, v, fv);
           }
-          if constexpr (R == 3)
-            h = pair_flux(za6<AI, P1>(pp[0], pp[1], pp[2], pp[3], pp[4], pp[5], rp),
-                          za6<AI, P1>(mm[0], mm[1], mm[2], mm[3], mm[4], mm[5], rp));
-          else
-            h = pair_flux_r<R>(za_r<R, AI, P1>(pp, rp), za_r<R, AI, P1>(mm, rp));
+          h = pair_flux_r<R>(za_r<R, AI, P1>(pp, rp), za_r<R, AI, P1>(mm, rp));
         }
-        fl[f][0] = 0.5 * h;
+        fl[f][0] = h;  // 2 F (the split without 1/2); 1/2 goes with 1/dx
       } else {
         const int kL = f + R - 1, kR = f + R;
         FaceState fs;
@@ -575,6 +605,18 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
           h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
           h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
           h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
+        } else if constexpr (R == 3) {
+          const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
+          double W[3][6], G[3][6];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            const int k = f + j;
+            project3(fs, pl[0][k], pl[1][k], pl[2][k], W[0][j], W[1][j], W[2][j]);
+            project3(fs, pl[6][k], pl[7][k], pl[8][k], G[0][j], G[1][j], G[2][j]);
+          }
+          h1 = field_flux<AI, P1>(W[0], G[0], A1, rp4);
+          h2 = field_flux<AI, P1>(W[1], G[1], A2, rp2);
+          h3 = field_flux<AI, P1>(W[2], G[2], A3, rp4);
         } else {
           const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
           double p1[N], p2[N], p3[N], m1[N], m2[N], m3[N];  // f^- mirrored
@@ -591,18 +633,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             p3[j] = fma(A3, w3, g3);
             m3[N - 1 - j] = fma(-A3, w3, g3);
           }
-          if constexpr (R == 3) {
-            h1 = pair_flux(za6<AI, P1>(p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], rp4),
-                           za6<AI, P1>(m1[0], m1[1], m1[2], m1[3], m1[4], m1[5], rp4));
-            h2 = pair_flux(za6<AI, P1>(p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], rp2),
-                           za6<AI, P1>(m2[0], m2[1], m2[2], m2[3], m2[4], m2[5], rp2));
-            h3 = pair_flux(za6<AI, P1>(p3[0], p3[1], p3[2], p3[3], p3[4], p3[5], rp4),
-                           za6<AI, P1>(m3[0], m3[1], m3[2], m3[3], m3[4], m3[5], rp4));
-          } else {
-            h1 = pair_flux_r<R>(za_r<R, AI, P1>(p1, rp4), za_r<R, AI, P1>(m1, rp4));
-            h2 = pair_flux_r<R>(za_r<R, AI, P1>(p2, rp2), za_r<R, AI, P1>(m2, rp2));
-            h3 = pair_flux_r<R>(za_r<R, AI, P1>(p3, rp4), za_r<R, AI, P1>(m3, rp4));
-          }
+          h1 = pair_flux_r<R>(za_r<R, AI, P1>(p1, rp4), za_r<R, AI, P1>(m1, rp4));
+          h2 = pair_flux_r<R>(za_r<R, AI, P1>(p2, rp2), za_r<R, AI, P1>(m2, rp2));
+          h3 = pair_flux_r<R>(za_r<R, AI, P1>(p3, rp4), za_r<R, AI, P1>(m3, rp4));
         }
         double F0, F1, F2;
         backproject3(fs, h1, h2, h3, F0, F1, F2);
@@ -614,7 +647,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
   }
   __syncthreads();
 
-  const double idx = 1.0 / a.dx;
+  // The faces hold 4 F (Euler, backproject3) or 2 F (a scalar: the split
+  // without 1/2), so that factor goes with 1/dx.
+  const double idx = (NC == 3 ? 0.25 : 0.5) / a.dx;
   unsigned long long m3v[3] = {0ull, 0ull, 0ull};
   const bool want_alpha = (NC == 3 || a.system >= 2) && (a.mode == 0) && (a.alpha_out != nullptr);
   if (tid < T && i0 + tid < nx) {
@@ -638,7 +673,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
       m3v[0] = okey(uo[0]);
       m3v[1] = okey(-uo[0]);
     } else if (want_alpha) {
-      const double ir = 1.0 / uo[0];
+      const double ir = rcp_pos(uo[0]);
       const double u = uo[1] * ir;
       const double p = gm1 * (uo[NC - 1] - 0.5 * (uo[1] * u));
       if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, 0, gi);

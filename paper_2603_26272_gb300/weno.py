@@ -100,6 +100,13 @@ def lib():
         L.weno_version.restype = ctypes.c_char_p
         L.weno_version.argtypes = []
         L.weno_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, _DP, _VP]
+        L.weno_dd_begin.argtypes = [_DESCP, _I64, _VP, _VP, _VP, _VP, _SZ, _VP]
+        L.weno_dd_speeds.argtypes = [_DESCP, _I64, ctypes.c_int, _VP, _SZ,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+        L.weno_dd_stage.argtypes = [_DESCP, _I64, ctypes.c_int, _VP, _D, _VP, _VP, _VP, _VP, _VP,
+                                    _SZ, _VP]
+        for name in ("weno_dd_begin", "weno_dd_speeds", "weno_dd_stage"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("weno_wavespeeds", "weno_rhs", "weno_step", "weno_solve", "weno_solve_host",
                      "weno_sync_status", "weno_step_host", "weno_fma_rate"):
             getattr(L, name).restype = ctypes.c_int
@@ -255,6 +262,36 @@ def step_host(desc, U_host, dt=0.0, ws=None, stream=None, device=None):
 def sync_status(desc, ws, stream=None):
     _check(lib().weno_sync_status(ctypes.byref(desc), ctypes.c_void_p(ws.data_ptr()),
                                   ctypes.c_size_t(ws.numel()), _stream(stream)))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def dd_begin(desc, nrows, U, send_lo, send_hi, ws, stream=None):
+    """weno_dd_begin: local speed maxima of the strip U and its edge rows."""
+    _check(lib().weno_dd_begin(ctypes.byref(desc), int(nrows), _ptr(U), _ptr(send_lo),
+                               _ptr(send_hi), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                               _stream(stream)))
+
+
+def dd_speeds(desc, nrows, stage, ws):
+    """The strip's speed slot that `stage` reads, as an int64 view [nbatch, 8]
+    of the workspace (bit patterns of non-negative doubles: integer max is
+    the numeric max)."""
+    out = ctypes.c_void_p(0)
+    _check(lib().weno_dd_speeds(ctypes.byref(desc), int(nrows), int(stage), _ptr(ws),
+                                ctypes.c_size_t(ws.numel()), ctypes.byref(out)))
+    off = out.value - ws.data_ptr()
+    n = desc.nbatch * 8 * 8
+    return ws[off:off + n].view(torch.int64).view(desc.nbatch, 8)
+
+
+def dd_stage(desc, nrows, stage, U, dt, halo_lo, halo_hi, send_lo, send_hi, ws, stream=None):
+    """weno_dd_stage: Runge-Kutta stage `stage` of the strip U."""
+    _check(lib().weno_dd_stage(ctypes.byref(desc), int(nrows), int(stage), _ptr(U), float(dt),
+                               _ptr(halo_lo), _ptr(halo_hi), _ptr(send_lo), _ptr(send_hi),
+                               _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream)))
 
 
 FMA_KINDS = {"fp64": 0, "fp64_short_mantissa": 1, "fp32": 2}

@@ -421,6 +421,23 @@ def test_eps_mu0_at_their_lower_limits(eps, mu0, order):
         weno.rhs(_desc(w, {"order": order, "eps": eps, "mu0": mu0 / 10}), to_gpu(U))
 
 
+@pytest.mark.parametrize("scale_exp", [40, -40])
+@pytest.mark.parametrize("order", [6, 8])
+def test_without_ai_on_large_and_small_data(scale_exp, order):
+    """Without Ai (mu = 1) the sensitivity term is the absolute 4 eps, so on
+    data of size 2^40 a flat substencil's indicator is ~1e-63 of the largest
+    one: the weights' rescaled indicators are floored (at 2^-166, 2^-125 for
+    order 8) to keep their products normal.  Against the oracle per stage."""
+    w = wl.quadrant_2d(n=40, seed=7)
+    c = 2.0 ** scale_exp
+    d = _desc(w, {"order": order, "ai": False})
+    g = ora_grid(w, d, order=order)
+    U = np.ascontiguousarray(w["U"]) * c
+    L_g = weno.rhs(d, to_gpu(U)).cpu().numpy()
+    assert np.isfinite(L_g).all()
+    assert rel_err(L_g, oracle.rhs(g, U)) <= STAGE_TOL
+
+
 def test_gpu_invariants_mirror_reduction_transpose():
     """Invariants of the GPU path itself (the oracle's pins, here on the GPU):
     mirror symmetry x -> -x, u -> -u in 1D; 2D data independent of y give

@@ -165,3 +165,71 @@ def test_flux_projection_from_state_projection():
     kern = sp.Matrix([uj * w[0] + (p * z - p / c), uj * w[1] - p * z, uj * w[2],
                       uj * w[3] + (p * z + p / c)])
     assert sp.simplify(kern - project4(*F)) == sp.zeros(4, 1)
+
+
+def test_weights_as_product_plus_tau_times_cofactor():
+    # a_k = (b_k + T) prod_{j != k} b_j = P + T Q_k, P = prod_j b_j, Q_k = P / b_k
+    b = sp.symbols("b0:4", positive=True)
+    T = sp.symbols("T", positive=True)
+    P = b[0] * b[1] * b[2] * b[3]
+    Q = [b[1] * (b[2] * b[3]), b[0] * (b[2] * b[3]), b[3] * (b[0] * b[1]), b[2] * (b[0] * b[1])]
+    for k in range(4):
+        assert sp.expand((b[k] + T) * Q[k] - (P + T * Q[k])) == 0
+
+
+def test_backprojection_returns_four_times_the_flux():
+    un, ut, c, g = sp.symbols("u_n u_t c gamma", positive=True)
+    q2 = un ** 2 + ut ** 2
+    H = c ** 2 / (g - 1) + q2 / 2
+    R = sp.Matrix([[1, 1, 0, 1],
+                   [un - c, un, 0, un + c],
+                   [ut, ut, 1, ut],
+                   [H - un * c, q2 / 2, ut, H + un * c]])
+    h = sp.symbols("h1:5")
+    e = sp.Matrix([h[0] / 4, h[1] / 2, h[2] / 2, h[3] / 4])
+    h14 = h[0] + h[3]
+    S = 2 * h[1] + h14
+    D = h[3] - h[0]
+    h3x2 = 2 * h[2]
+    kern = sp.Matrix([S, un * S + c * D, ut * S + h3x2,
+                      H * h14 + un * c * D + q2 * h[1] + ut * h3x2])
+    assert sp.simplify(kern - 4 * R * e) == sp.zeros(4, 1)
+    # 1D
+    u = sp.symbols("u")
+    H1 = c ** 2 / (g - 1) + u ** 2 / 2
+    R1 = sp.Matrix([[1, 1, 1], [u - c, u, u + c], [H1 - u * c, u ** 2 / 2, H1 + u * c]])
+    e1 = sp.Matrix([h[0] / 4, h[1] / 2, h[2] / 4])
+    h13 = h[0] + h[2]
+    S1 = 2 * h[1] + h13
+    D1 = h[2] - h[0]
+    kern1 = sp.Matrix([S1, u * S1 + c * D1, H1 * h13 + u * c * D1 + u ** 2 * h[1]])
+    assert sp.simplify(kern1 - 4 * R1 * e1) == sp.zeros(3, 1)
+
+
+def test_split_applied_to_differences():
+    # f+ = g + A w on (i-2 .. i+3); f- = g - A w read from i+3 down to i-2
+    w = sp.symbols("w0:6")
+    g = sp.symbols("g0:6")
+    A = sp.symbols("A")
+    fp = [g[j] + A * w[j] for j in range(6)]
+    fm = [g[5 - j] - A * w[5 - j] for j in range(6)]  # mirrored stencil
+    dw = [w[j + 1] - w[j] for j in range(5)]
+    dg = [g[j + 1] - g[j] for j in range(5)]
+    dp = [A * dw[j] + dg[j] for j in range(5)]
+    dm = [None] * 5
+    for j in range(5):
+        dm[4 - j] = A * dw[j] - dg[j]
+    for j in range(5):
+        assert sp.expand(dp[j] - (fp[j + 1] - fp[j])) == 0
+        assert sp.expand(dm[j] - (fm[j + 1] - fm[j])) == 0
+    base = -A * dw[2] + (g[2] + g[3])
+    assert sp.expand(base - (fp[2] + fm[2])) == 0
+
+
+def test_cubic_newton_reciprocal_step():
+    # r1 = r0 + r0 (e + e^2), e = 1 - x r0  =>  1 - x r1 = e^3: a seed within
+    # 2^-22 of 1/x gives 1/x to 2^-66 before the final roundings
+    x, r0 = sp.symbols("x r0", positive=True)
+    e = 1 - x * r0
+    r1 = r0 + r0 * (e + e ** 2)
+    assert sp.expand((1 - x * r1) - e ** 3) == 0
