@@ -247,17 +247,24 @@ def configs_1d(weno, wl, torch):
     return out
 
 
-# admission budget of the engine: admitted solves' cost per step, in 2D FP64
-# cells (about 2 tiles per SM of 16x16 cells on 152 SMs, with a margin).
+# admission budget of the engine when every solve goes through it (policy
+# "engine"): admitted solves' cost per step, in 2D FP64 cells (about 2 tiles
+# per SM of 16x16 cells on 152 SMs, with a margin).
 WORK_BUDGET = 250e3
 
 
-def serving(n_requests=100, seed=5, loads=(1.0, 1.25), mix="small"):
-    """Configuration 5, scaled to about a minute: a seeded stream of mixed
-    1D/2D, FP64/FP32-reconstruction solves.  The offered Poisson rate is set
-    to `loads` x the one-at-a-time capacity (measured first on the same GPU);
-    at each load the same arrivals are served one at a time (weno_solve, FIFO)
-    and by the continuous-batching engine."""
+def serving(n_requests=64, seed=5, loads=(1.0, 1.25), mix="full", policy="two_lane",
+            capacity=False, large_workers=2):
+    """Configuration 5: a seeded Poisson stream of mixed 1D/2D, FP64/FP32-
+    reconstruction solves of the configured sizes (2D sides 128..1024, 1D N
+    256..16384, 100..1000 steps), n_requests of them (the configured 2000
+    take about 20 minutes per pass).  The offered rate is `loads` x the
+    one-at-a-time capacity, measured first on the same GPU; at each load the
+    same arrivals are served one at a time (weno_solve, first come first
+    served) and by the serving loop (`policy`: "two_lane" -- solves that fill
+    the GPU alone one at a time on a low-priority stream, all others in the
+    continuous-batching engine on a high-priority stream -- or "engine",
+    every solve in the engine under a work budget)."""
     import torch
     from paper_2603_26272_gb300 import serve
     if mix == "full":
@@ -271,11 +278,22 @@ def serving(n_requests=100, seed=5, loads=(1.0, 1.25), mix="small"):
     calib_thr = serve.summarize(reqs)["throughput_cell_updates_per_s"]
     free = torch.cuda.mem_get_info()[0]
     eng = serve.Engine(arena_bytes=int(min(8 << 30, free // 2)), max_slots=256)
-    out = {"workload": "%d requests: 50%% 1D Euler Riemann (N log-uniform %d..%d), 50%% 2D "
-                       "quadrant (side in %s); 50%% FP64, 50%% FP32-recon; %d..%d steps each; "
-                       "Poisson arrivals (seed %d)" % (n_requests, n1d[0], n1d[1], list(sides),
-                                                       steps[0], steps[1], seed),
-           "work_budget_cell_units": WORK_BUDGET, "loads": []}
+
+    def run(rs):
+        if policy == "two_lane":
+            return serve.serve_two_lane(eng, rs, large_workers=large_workers)
+        return serve.serve_continuous(eng, rs, steps_per_poll=2, work_budget=WORK_BUDGET)
+
+    out = {"workload": "%d requests (of the configured 2000; the rest scaled as configured): "
+                       "50%% 1D Euler Riemann (N log-uniform %d..%d), 50%% 2D quadrant (side in "
+                       "%s); 50%% FP64, 50%% FP32-recon; %d..%d steps each; Poisson arrivals "
+                       "(seed %d)" % (n_requests, n1d[0], n1d[1], list(sides), steps[0], steps[1],
+                                      seed),
+           "policy": policy,
+           "large_lane_tiles": serve.full_wave_tiles() if policy == "two_lane" else None,
+           "large_lane_workers": large_workers if policy == "two_lane" else None,
+           "work_budget_cell_units": WORK_BUDGET if policy == "engine" else None,
+           "mean_service_s_one_at_a_time": float(np.mean(service)), "loads": []}
     for load in loads:
         rate = load / float(np.mean(service))
         gaps = np.random.default_rng(seed + 1).exponential(1.0 / rate, size=len(reqs))
@@ -286,8 +304,9 @@ def serving(n_requests=100, seed=5, loads=(1.0, 1.25), mix="small"):
         base = serve.summarize(serve.serve_one_at_a_time(reqs))
         for r in reqs:
             r.result = {}
-        cont = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2,
-                                                      work_budget=WORK_BUDGET))
+        cont = serve.summarize(run(reqs))
+        if policy == "two_lane":
+            cont["large_lane_requests"] = sum(1 for r in reqs if r.result.get("lane") == "large")
         out["loads"].append({
             "offered_load_vs_one_at_a_time": load, "offered_rate_per_s": rate,
             "one_at_a_time": base, "continuous_batching": cont,
@@ -295,18 +314,59 @@ def serving(n_requests=100, seed=5, loads=(1.0, 1.25), mix="small"):
                                  / base["throughput_cell_updates_per_s"]),
             "p50_ratio": cont["p50_latency_s"] / base["p50_latency_s"],
             "p99_ratio": cont["p99_latency_s"] / base["p99_latency_s"]})
-    # capacity: every request present at t = 0, engine versus the back-to-back
-    # one-at-a-time calibration run above
-    for r in reqs:
-        r.arrival = 0.0
-        r.result = {}
-    sat = serve.summarize(serve.serve_continuous(eng, reqs, steps_per_poll=2,
-                                                 work_budget=WORK_BUDGET))
+    if capacity:
+        # every request present at t = 0, against the back-to-back
+        # one-at-a-time calibration run above
+        for r in reqs:
+            r.arrival = 0.0
+            r.result = {}
+        sat = serve.summarize(run(reqs))
+        out.update({"capacity_one_at_a_time_cell_updates_per_s": calib_thr,
+                    "capacity_continuous_cell_updates_per_s": sat["throughput_cell_updates_per_s"],
+                    "capacity_ratio": sat["throughput_cell_updates_per_s"] / calib_thr})
     eng.close()
-    out.update({"capacity_one_at_a_time_cell_updates_per_s": calib_thr,
-                "capacity_continuous_cell_updates_per_s": sat["throughput_cell_updates_per_s"],
-                "capacity_ratio": sat["throughput_cell_updates_per_s"] / calib_thr})
     return out
+
+
+def kernel_tour(weno, wl, torch, reps=3):
+    """Each kernel family of the library a few times on its configuration's
+    data, for per-kernel ncu captures (-k <kernel> -c 1): the 2D stage in
+    FP64 and FP32 reconstruction (2048^2 quadrant), the 1D tile kernel (64
+    Riemann problems x 1600), the 1D lane layout (shock-density N = 1600),
+    the wavespeed pass, a domain-split stage (two strips) and the serving
+    engine (a few small solves).  Prints one line per family."""
+    from paper_2603_26272_gb300 import decomp, serve
+    w = wl.quadrant_2d(n=N_GRID, seed=SEED)
+    for prec in ("fp64", "fp32_recon"):
+        d = weno.desc_for(w, precision=prec)
+        U = torch.from_numpy(w["U"]).cuda()
+        ws = weno.workspace(d)
+        for _ in range(reps):
+            weno.step(d, U, ws=ws, sync=False)
+        weno.sync_status(d, ws)
+        log("tour: 2D stage %s" % prec)
+        del U, ws
+    for w1 in (wl.riemann_batch(nbatch=64, n=1600, seed=2), wl.shock_density(n=1600)):
+        d = weno.desc_for(w1)
+        U = torch.from_numpy(np.ascontiguousarray(w1["U"])).cuda()
+        ws = weno.workspace(d)
+        for _ in range(reps):
+            weno.step(d, U, ws=ws, sync=False)
+        weno.sync_status(d, ws)
+        log("tour: 1D nbatch %d" % d.nbatch)
+    d = weno.desc_for(w)
+    grp = decomp.StripGroup(d, 2)
+    parts = grp.split(torch.from_numpy(w["U"]).cuda())
+    for _ in range(reps):
+        grp.step(parts)
+    torch.cuda.synchronize()
+    log("tour: strips")
+    del parts, grp
+    reqs = serve.make_requests(8, seed=7, sides_2d=(128, 192), n1d=(256, 4096), steps=(20, 40))
+    eng = serve.Engine(arena_bytes=1 << 30, max_slots=16)
+    serve.serve_continuous(eng, reqs, steps_per_poll=2)
+    eng.close()
+    log("tour: engine")
 
 
 def cpu_baseline(seconds, window=256):
@@ -391,10 +451,16 @@ def main():
     ap.add_argument("--no-precision-modes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-orders", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=100)
-    ap.add_argument("--serving-mix", choices=["small", "full"], default="small",
-                    help="small: 2D sides 128-256, 100-300 steps (about a minute); full: the "
-                         "configured sides 128-1024 and 100-1000 steps")
+    ap.add_argument("--serving-requests", type=int, default=64)
+    ap.add_argument("--serving-mix", choices=["small", "full"], default="full",
+                    help="full: the configured 2D sides 128-1024 and 100-1000 steps; small: 2D "
+                         "sides 128-256, 100-300 steps")
+    ap.add_argument("--serving-policy", choices=["two_lane", "engine"], default="two_lane")
+    ap.add_argument("--kernel-tour", action="store_true",
+                    help="run each kernel family a few times (for per-kernel ncu captures) and exit")
+    ap.add_argument("--serving-large-workers", type=int, default=2)
+    ap.add_argument("--serving-capacity", action="store_true",
+                    help="also serve every request at t = 0 (one more pass)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -411,6 +477,9 @@ def main():
     from paper_2603_26272_gb300 import workloads as wl
 
     torch.cuda.set_device(local)
+    if args.kernel_tour:
+        kernel_tour(weno, wl, torch)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -544,7 +613,9 @@ def main():
         result["gpu_launches_scheme_orders"] = 4 * 4 * (4 + 3)
     if not args.no_serving and rank == 0:
         log("serving stream ...")
-        result["serving"] = serving(args.serving_requests, mix=args.serving_mix)
+        result["serving"] = serving(args.serving_requests, mix=args.serving_mix,
+                                    policy=args.serving_policy, capacity=args.serving_capacity,
+                                    large_workers=args.serving_large_workers)
     if rank == 0 and not args.no_cpu_baseline:
         log("timing the CPU oracle on the host cores ...")
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -248,8 +248,11 @@ weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, double *dUdt, 
  * tables; the rest is a heap for the slots' states (weno_engine_slot_bytes
  * each).  Admission fails with WENO_ERR_NOMEM when no slot, work-list entry
  * or heap block is free; the engine never calls the allocator.
- * The engine works on a CUDA stream of its own; run() is asynchronous,
- * admit/poll/retire synchronise it.  One host thread per engine.
+ * The engine works on a CUDA stream of its own, created with the device's
+ * highest stream priority (a large solve the caller runs beside it on a
+ * stream of lower priority yields the SMs to the engine's blocks as its own
+ * blocks finish); run() is asynchronous, admit/poll/retire synchronise it.
+ * One host thread per engine.
  * --------------------------------------------------------------------------- */
 typedef struct weno_engine weno_engine;
 

@@ -248,7 +248,13 @@ weno_status weno_engine_create(void *arena, size_t arena_bytes, int max_slots, i
   std::memset(E->mirror.data(), 0, sizeof(SlotDev) * max_slots);
   E->free_blocks[L.total] = (arena_bytes - L.total) & ~size_t(255);
   (void)stream;  // the engine works on a stream of its own (a graph needs a capturable stream)
-  cudaError_t e = cudaStreamCreateWithFlags(&E->s, cudaStreamNonBlocking);
+  // ... of the highest priority: while a caller runs a large solve on a
+  // stream of lower priority, the block scheduler hands the engine's blocks
+  // the next free places on the SMs, so the small solves it holds keep
+  // their pace instead of waiting for the large one to finish
+  int prio_least = 0, prio_greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&E->s, cudaStreamNonBlocking, prio_greatest);
   if (e != cudaSuccess) {
     delete E;
     return ecuda(e, "cudaStreamCreateWithFlags");

@@ -2,12 +2,15 @@
 
 Requests are independent Euler solves (1D or 2D, FP64 or FP32
 reconstruction, each to its own final time) arriving as a Poisson stream.
-`serve_continuous` admits arrived requests whenever the engine has a free
-slot, work-list room and a free block of its device arena (admission by free
-HBM, smallest-fit bypass when the head of the queue does not fit), advances
-all admitted solves together a few engine steps at a time, and retires the
-finished ones.  `serve_one_at_a_time` is the baseline: the same requests, in
-arrival order, each solved alone with weno_solve on the same GPU.
+`serve_two_lane` is the serving loop: solves large enough to fill the GPU
+alone run one at a time on a low-priority stream, and every other solve is
+admitted to the continuous-batching engine (high-priority stream) as soon as
+it arrives and the engine has room -- a free slot, work-list room and a free
+block of its device arena (admission by free HBM) -- and advances there
+with the other small solves.  `serve_continuous` puts every solve through
+the engine (first come first served under a work budget).
+`serve_one_at_a_time` is the baseline: the same requests, in arrival order,
+each solved alone with weno_solve on the same GPU.
 
 Argument marshalling and queueing only; every step of the method runs in the
 CUDA kernels of libweno.so.
@@ -292,6 +295,127 @@ def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, work
                 mark_fast()
         elif pending:
             time.sleep(max(0.0, min(pending[0].arrival - (clock() - t0), 0.01)))
+    for r in requests:
+        r.result["arrival"] = r.arrival
+    return requests
+
+
+def engine_tiles(r):
+    """Work-list tiles of a request in the engine (16 x 16 cells in 2D, 127
+    cells in 1D)."""
+    d = r.desc
+    if d.ndim == 2:
+        return ((d.nx + 15) // 16) * ((d.ny + 15) // 16)
+    return (d.nx + 126) // 127
+
+
+def full_wave_tiles(device=None):
+    """Tiles the GPU runs at once: 3 blocks of 16 x 16 cells per SM."""
+    return 3 * torch.cuda.get_device_properties(device or torch.cuda.current_device()).multi_processor_count
+
+
+def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_per_poll=2,
+                   keep_states=False, clock=time.perf_counter):
+    """Continuous batching with a lane for the solves that fill the GPU alone.
+
+    A 2D solve of at least `large_tiles` tiles (default: one full wave of
+    the GPU, so 384^2 and up) keeps every SM busy by itself: sharing the GPU
+    with other such solves would only stretch each of them.  Those run one
+    at a time, first come first served, through weno_solve on a stream of
+    the lowest priority, in worker threads: `large_workers` of them, so
+    that a second large solve fills the SMs the first one's last wave of
+    tiles leaves idle (a 384^2 stage is 1.26 waves of the GPU, 512^2 2.25);
+    its blocks queue behind the older solve's, which keeps its pace.  Every
+    other solve (1D, small
+    2D) is admitted to the engine as soon as it arrives and there is room;
+    the engine's stream has the highest priority, so its blocks take the
+    places the large solve's blocks free and the small solves keep roughly
+    the pace they have alone.  A small solve therefore never waits for a
+    large one, and the GPU time a small solve alone would leave idle (a
+    latency-bound stage on a few SMs) goes to the large solve.
+
+    Fills request.result like serve_continuous (plus "lane")."""
+    import queue
+    import threading
+
+    if large_tiles is None:
+        large_tiles = full_wave_tiles()
+    pending = deque(sorted(requests, key=lambda r: r.arrival))
+    waiting = []
+    active = {}
+    big_q = queue.Queue()
+    t0 = clock()
+    device = torch.cuda.current_device()
+    errors = []
+
+    def big_lane():
+        torch.cuda.set_device(device)
+        stream = torch.cuda.Stream(device=device, priority=0)  # lowest priority
+        while True:
+            r = big_q.get()
+            if r is None:
+                return
+            try:
+                with torch.cuda.stream(stream):
+                    U = torch.from_numpy(r.U).to(device)
+                    stream.synchronize()
+                    r.result["admit"] = clock() - t0
+                    try:
+                        t, n = weno.solve(r.desc, U, r.t_final, stream=stream)
+                        r.result.update({"t": t[0], "steps": n[0], "status": 0})
+                    except weno.WenoError as e:
+                        r.result.update({"t": float("nan"), "steps": 0, "status": e.code})
+                    if keep_states:
+                        r.result["U"] = U.cpu().numpy()
+                r.result["done"] = clock() - t0
+            except Exception as e:  # noqa: BLE001 -- reported by the main thread
+                errors.append(e)
+                r.result.update({"done": clock() - t0, "status": -1, "steps": 0})
+
+    workers = [threading.Thread(target=big_lane, daemon=True) for _ in range(large_workers)]
+    for wk in workers:
+        wk.start()
+    try:
+        while pending or waiting or active:
+            now = clock() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending.popleft()
+                r.result["lane"] = "large" if (r.desc.ndim == 2 and engine_tiles(r) >= large_tiles) \
+                    else "engine"
+                if r.result["lane"] == "large":
+                    big_q.put(r)
+                else:
+                    waiting.append(r)
+            still = []
+            for r in waiting:
+                slot = engine.admit(r.desc, r.U, r.t_final)
+                if slot is None:
+                    still.append(r)
+                    continue
+                r.result["admit"] = clock() - t0
+                active[slot] = r
+            waiting = still
+            if waiting and not active:
+                raise RuntimeError("request %d does not fit the empty engine (arena or work list "
+                                   "too small)" % waiting[0].rid)
+            if active:
+                engine.run(steps_per_poll)
+                done, _ = engine.poll()
+                for slot in done:
+                    U, t, n, code = engine.retire(slot, want_state=keep_states)
+                    r = active.pop(slot)
+                    r.result.update({"done": clock() - t0, "t": t, "steps": n, "status": code})
+                    if keep_states:
+                        r.result["U"] = U
+            elif pending:
+                time.sleep(max(0.0, min(pending[0].arrival - (clock() - t0), 0.005)))
+    finally:
+        for _ in workers:
+            big_q.put(None)
+        for wk in workers:
+            wk.join()
+    if errors:
+        raise errors[0]
     for r in requests:
         r.result["arrival"] = r.arrival
     return requests
