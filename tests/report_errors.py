@@ -8,9 +8,12 @@ markdown table (relative L1 = sum|a - b| / sum|b|, relative L_inf =
 max|a - b| / max|b|).  Where an exact solution exists (linear advection, the
 Riemann problems) the oracle's own error against it is printed too.  For the
 1D runs the last columns give the oracle's own spread: the same run from
-the input times (1 +- 1e-16) (random signs) against the unperturbed run.
-With p = 1 and eps = 1e-40 some runs amplify rounding far above 1e-10; the
-GPU's difference is to be read against that spread.
+the input times (1 +- 1e-16) (random signs), and the same run in the oracle
+build whose final sums are added in the opposite order, each against the
+stock run, and whether the FP64 GPU result meets 1e-10 and the full-run
+bound max(1e-10, 4 x spread).  With p = 1 and eps = 1e-40 some runs amplify
+rounding far above 1e-10; the GPU's difference is to be read against that
+spread.
 Not collected by pytest (a measurement, about 5 minutes of oracle time); its
 output is summarised in profiles/errors_by_config.md.
 
@@ -52,7 +55,9 @@ def grid_of(d):
 
 
 def oracle_spread(w, n_steps, t_final, order=6):
-    """The oracle from a rounding-level perturbed input (its own CFL steps)."""
+    """The oracle's own rounding floor: the stock run, the run from the input
+    times (1 +- 1e-16) and the run in the reversed-summation build (each with
+    its own CFL steps)."""
     d = weno.desc_for(w, order=order)
     g = grid_of(d)
     U0 = np.ascontiguousarray(w["U"])
@@ -68,7 +73,11 @@ def oracle_spread(w, n_steps, t_final, order=6):
         return U
 
     rng = np.random.default_rng(1)
-    return go(U0), go(U0 * (1 + 1e-16 * rng.choice([-1.0, 1.0], size=U0.shape)))
+    base = go(U0)
+    pert = go(U0 * (1 + 1e-16 * rng.choice([-1.0, 1.0], size=U0.shape)))
+    with oracle.rounding_variant("reversed"):
+        rev = go(U0)
+    return base, pert, rev
 
 
 def run(w, t_final=None, steps=None, order=6, with_fp32=True):
@@ -102,6 +111,10 @@ NAMES = {1: ["u"], 3: ["rho", "rho u", "E"], 4: ["rho", "rho u", "rho v", "E"]}
 
 
 def table(title, U_o, a, b, extra="", spread=None):
+    """One markdown table per configuration.  With `spread` (the oracle run
+    from the perturbed input and in the reversed-summation build) the
+    columns give both spreads and whether the FP64 GPU result meets the
+    flat 1e-10 bound and the full-run bound max(1e-10, 4 x spread)."""
     nc = U_o.shape[1]
     print("\n### %s\n" % title)
     if extra:
@@ -112,16 +125,27 @@ def table(title, U_o, a, b, extra="", spread=None):
         head += " FP32-recon rel L1 | FP32-recon rel Linf |"
         sep += "---|---|"
     if spread is not None:
-        head += " oracle spread rel L1 | oracle spread rel Linf |"
-        sep += "---|---|"
+        head += (" oracle spread, input x(1+-1e-16), rel Linf | oracle spread, reversed sums, "
+                 "rel Linf | meets 1e-10 | meets the full-run bound |")
+        sep += "---|---|---|---|"
+    else:
+        head += " meets 1e-10 |"
+        sep += "---|"
     print(head)
     print(sep)
     for k in range(nc):
-        row = "| %s | %.2e | %.2e |" % ((NAMES[nc][k],) + rel(a, U_o, k))
+        e1, einf = rel(a, U_o, k)
+        row = "| %s | %.2e | %.2e |" % (NAMES[nc][k], e1, einf)
         if b is not None:
             row += " %.2e | %.2e |" % rel(b, U_o, k)
         if spread is not None:
-            row += " %.2e | %.2e |" % rel(spread[1], spread[0], k)
+            sp_p = rel(spread[1], spread[0], k)[1]
+            sp_r = rel(spread[2], spread[0], k)[1]
+            bound = max(1e-10, 4.0 * max(sp_p, sp_r))
+            row += " %.2e | %.2e | %s | %s |" % (sp_p, sp_r, "yes" if einf <= 1e-10 else "no",
+                                                  "yes" if einf <= bound else "no")
+        else:
+            row += " %s |" % ("yes" if einf <= 1e-10 else "no")
         print(row)
     sys.stdout.flush()
 
