@@ -315,18 +315,21 @@ def full_wave_tiles(device=None):
 
 
 def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_per_poll=2,
-                   keep_states=False, clock=time.perf_counter):
+                   keep_states=False, chunk_steps=16, clock=time.perf_counter):
     """Continuous batching with a lane for the solves that fill the GPU alone.
 
     A 2D solve of at least `large_tiles` tiles (default: one full wave of
     the GPU, so 384^2 and up) keeps every SM busy by itself: sharing the GPU
     with other such solves would only stretch each of them.  Those run one
     at a time, first come first served, through weno_solve on a stream of
-    the lowest priority, in worker threads: `large_workers` of them, so
-    that a second large solve fills the SMs the first one's last wave of
-    tiles leaves idle (a 384^2 stage is 1.26 waves of the GPU, 512^2 2.25);
-    its blocks queue behind the older solve's, which keeps its pace.  Every
-    other solve (1D, small
+    low priority, in worker threads: `large_workers` of them, so that a
+    second large solve fills the SMs the first one's last wave of tiles and
+    its host round trips leave idle (a 384^2 stage is 1.26 waves of the GPU,
+    512^2 2.25).  The oldest large solve runs on a stream of higher priority
+    than the younger ones (each solve goes in chunks of `chunk_steps` steps,
+    weno_solve from the reached time, bitwise one call, and picks its stream
+    per chunk), so it keeps the pace it has alone and first come first served
+    holds for the large solves.  Every other solve (1D, small
     2D) is admitted to the engine as soon as it arrives and there is room;
     the engine's stream has the highest priority, so its blocks take the
     places the large solve's blocks free and the small solves keep roughly
@@ -348,29 +351,52 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
     device = torch.cuda.current_device()
     errors = []
 
+    order = []  # large solves in progress, oldest first
+    lock = threading.Lock()
+
     def big_lane():
         torch.cuda.set_device(device)
-        stream = torch.cuda.Stream(device=device, priority=0)  # lowest priority
+        # the oldest large solve on a stream above the others (still below
+        # the engine's), so it keeps the pace it has alone and the younger
+        # ones take only the places its blocks leave free
+        s_old = torch.cuda.Stream(device=device, priority=-1)
+        s_new = torch.cuda.Stream(device=device, priority=0)
         while True:
             r = big_q.get()
             if r is None:
                 return
+            with lock:
+                order.append(r.rid)
             try:
-                with torch.cuda.stream(stream):
+                with torch.cuda.stream(s_new):
                     U = torch.from_numpy(r.U).to(device)
-                    stream.synchronize()
-                    r.result["admit"] = clock() - t0
+                    ws = weno.workspace(r.desc, device=device)
+                s_new.synchronize()
+                r.result["admit"] = clock() - t0
+                t, steps, status = 0.0, 0, 0
+                while t < r.t_final:
+                    with lock:
+                        st = s_old if order[0] == r.rid else s_new
                     try:
-                        t, n = weno.solve(r.desc, U, r.t_final, stream=stream)
-                        r.result.update({"t": t[0], "steps": n[0], "status": 0})
+                        tt, nn = weno.solve(r.desc, U, r.t_final, t0=t, max_steps=chunk_steps,
+                                            ws=ws, stream=st, allow_max_steps=True)
                     except weno.WenoError as e:
-                        r.result.update({"t": float("nan"), "steps": 0, "status": e.code})
-                    if keep_states:
-                        r.result["U"] = U.cpu().numpy()
+                        status = e.code
+                        break
+                    t, steps = tt[0], steps + nn[0]
+                    if nn[0] == 0:
+                        break
+                r.result.update({"t": t if status == 0 else float("nan"), "steps": steps,
+                                 "status": status})
+                if keep_states:
+                    r.result["U"] = U.cpu().numpy()
                 r.result["done"] = clock() - t0
             except Exception as e:  # noqa: BLE001 -- reported by the main thread
                 errors.append(e)
                 r.result.update({"done": clock() - t0, "status": -1, "steps": 0})
+            finally:
+                with lock:
+                    order.remove(r.rid)
 
     workers = [threading.Thread(target=big_lane, daemon=True) for _ in range(large_workers)]
     for wk in workers:

@@ -215,14 +215,20 @@ def step(desc, U, dt=0.0, ws=None, stream=None, sync=True):
     return None
 
 
-def solve(desc, U, t_final, t0=0.0, max_steps=2 ** 62, ws=None, stream=None):
-    """Advance U in place to t_final; returns (t[nbatch], steps[nbatch])."""
+def solve(desc, U, t_final, t0=0.0, max_steps=2 ** 62, ws=None, stream=None,
+          allow_max_steps=False):
+    """Advance U in place from t0 to t_final; returns (t[nbatch], steps[nbatch]).
+    With allow_max_steps, stopping at max_steps before t_final is not an
+    error (continue with t0 = the returned t: the result is bitwise that of
+    one call)."""
     Up = _state(desc, U)
     ws, wp, wn = _ws(desc, ws, U.device)
     t = (ctypes.c_double * desc.nbatch)()
     n = (ctypes.c_int64 * desc.nbatch)()
-    _check(lib().weno_solve(ctypes.byref(desc), Up, float(t0), float(t_final), int(max_steps),
-                            t, n, wp, wn, _stream(stream)))
+    code = lib().weno_solve(ctypes.byref(desc), Up, float(t0), float(t_final), int(max_steps),
+                            t, n, wp, wn, _stream(stream))
+    if not (allow_max_steps and code == WENO_ERR_MAXSTEPS):
+        _check(code)
     return list(t), list(n)
 
 
