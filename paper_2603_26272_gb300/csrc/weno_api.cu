@@ -268,6 +268,12 @@ weno_status read_status(const Ctx &c) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync status");
   e = cudaStreamSynchronize(c.s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (h.code == 5) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "a tile's shared-memory copy did not complete (problem %lld, "
+                  "tile at j=%lld, i=%lld)", h.b, h.j, h.i);
+    return fail(WENO_ERR_TIMEOUT, buf);
+  }
   if (h.code != 0) {
     static const char *where[] = {"wavespeeds", "stage 1", "stage 2", "stage 3", "rhs"};
     char buf[256];

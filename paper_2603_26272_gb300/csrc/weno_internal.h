@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace weno {
@@ -54,6 +55,9 @@ struct StageArgs {
   // output's first / last r rows are copied into send_lo / send_hi (same layout).
   const double *halo_lo, *halo_hi;
   double *send_lo, *send_hi;
+  // set by the 2D launcher: interior tiles stage by TMA through the tensor
+  // map passed beside these arguments
+  int use_tma;
 };
 
 // Wavespeed reduction of U into alpha_out (which must be zero), optional dt.
@@ -104,6 +108,14 @@ size_t engine_smem_bytes();
 long long engine_tiles_of(int ndim, long long nx, long long ny);
 cudaError_t engine_prepare();  // kernel attributes; call before capturing
 cudaError_t launch_engine_stage(const EngineArgs &e, int grid, cudaStream_t s);
+
+// Tensor map of a 2D stage input U [nbatch][4][ny][nx] as a 3D tensor
+// (x, y, plane of a problem) with a box of bw x bh x 4 doubles; false when a
+// tiled copy cannot address it (nx odd: rows are not multiples of 16 bytes;
+// U not 16-byte aligned; the grid smaller than the box; no encoder in the
+// driver), and the launch then stages with plain loads.
+bool encode_state_map(const double *U, long long nbatch, long long ny, long long nx, int bw,
+                      int bh, CUtensorMap *out);
 
 cudaError_t launch_alpha(const AlphaArgs &a, cudaStream_t s);
 cudaError_t launch_stage(const StageArgs &a, cudaStream_t s);

@@ -3,6 +3,8 @@
 // host-side launchers for GB300 (sm_103a).  The tile kernels themselves are in
 // weno_tiles.cuh; the schemes of other orders are instantiated in
 // weno_orders.cu.
+#include <mutex>
+
 #include "weno_tiles.cuh"
 
 namespace weno {
@@ -144,6 +146,7 @@ __device__ __forceinline__ StageArgs slot_stage_args(const SlotDev &S, int stage
   a.t_final = S.t_final;
   a.halo_lo = a.halo_hi = nullptr;
   a.send_lo = a.send_hi = nullptr;
+  a.use_tma = 0;
   a.t = S.clock;
   a.tnext = S.clock + 1;
   a.dt = S.clock + 2;
@@ -198,6 +201,44 @@ cudaError_t launch_order(const StageArgs &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+namespace {
+// cuTensorMapEncodeTiled, looked up once through the runtime (the library
+// links no driver library of its own)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+}  // namespace
+
+bool encode_state_map(const double *U, long long nbatch, long long ny, long long nx, int bw,
+                      int bh, CUtensorMap *out) {
+  if (!U || (nx & 1) || (reinterpret_cast<uintptr_t>(U) & 15) || nx < bw || ny < bh) return false;
+  if (nx > (1LL << 31) || ny > (1LL << 31) || nbatch * 4 > (1LL << 31)) return false;
+  EncodeTiledFn fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(nbatch * 4)};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 8, (cuuint64_t)nx * (cuuint64_t)ny * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 4};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double *>(U), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 cudaError_t launch_stage(const StageArgs &a, cudaStream_t s) {
   const bool p1 = (a.p == 1.0);

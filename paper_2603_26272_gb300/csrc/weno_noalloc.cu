@@ -146,6 +146,7 @@ extern "C" weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, dou
   e = cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return say(WENO_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+  if (h.code == 5) return say(WENO_ERR_TIMEOUT, "a tile's shared-memory copy did not complete");
   if (h.code != 0) {
     char buf[192];
     std::snprintf(buf, sizeof(buf), "nonphysical state in problem %lld, cell (j=%lld, i=%lld)", h.b,

@@ -24,6 +24,9 @@
 #pragma once
 #include <cfloat>
 #include <cmath>
+#include <cstring>
+
+#include <cuda.h>  // CUtensorMap (the type only; the encoder is fetched at run time)
 
 #include "weno_device.cuh"
 #include "weno_internal.h"
@@ -175,6 +178,57 @@ __device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long
 }
 
 // ---------------------------------------------------------------------------
+// Tensor-memory-accelerator (TMA) staging of a 2D tile: one bulk tensor copy
+// brings the conserved variables of the tile and its halo -- a box of
+// (TX + 2 XO) x (TY + 2 R) cells of all four planes of the problem -- from
+// global into shared memory, completing on an mbarrier.  XO is R rounded up
+// to even, so the box starts at x = i0 - XO, a multiple of 2 doubles: the
+// 16-byte alignment a tiled copy needs for its innermost coordinate.  Only
+// interior tiles (the whole box inside the grid) use it; tiles that need
+// ghost cells (clamp, wrap, halo rows) load with plain indexed loads.
+// ---------------------------------------------------------------------------
+template <int R> struct TmaBox {
+  static constexpr int XO = (R + 1) & ~1;
+};
+
+template <int TX, int TY, int R>
+__host__ __device__ constexpr size_t tma_box_bytes() {
+  return sizeof(double) * 4 * (TX + 2 * TmaBox<R>::XO) * (TY + 2 * R);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Issue the copy (thread 0 only): barrier armed with the byte count first.
+__device__ __forceinline__ void tma_issue_box(const CUtensorMap *tm, unsigned bar, void *dst,
+                                              int x, int y, int z, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(tm), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// SM clock cycles a TMA wait may take before it gives up (about 1 ms at
+// 2 GHz; the copy of one box takes microseconds).
+constexpr long long kTmaWaitCycles = 2000000;
+
+// ---------------------------------------------------------------------------
 // 2D Euler stage kernel.
 // Shared planes per staged cell: 0 rho, 1 rho u, 2 rho v, 3 E, 4 u, 5 v, 6 H,
 // 7 sqrt(rho), 8 p (the fluxes are projected from u, v, p: project_flux4).
@@ -185,17 +239,28 @@ __device__ void block_max_atomic(unsigned long long (&v)[NV], unsigned long long
 constexpr int kPlanes2D = 9;
 
 template <int TX, int TY, int R = 3>
-constexpr size_t smem_euler2d() {
+__host__ __device__ constexpr size_t smem_euler2d() {
   return sizeof(double) *
          (kPlanes2D * (TX + 2 * R) * (TY + 2 * R) + 4 * ((TX + 1) * TY + TX * (TY + 1)));
 }
 
+// Dynamic shared memory of a tile that may stage by TMA: the planes and
+// faces, then the box, 128-byte aligned.
+template <int TX, int TY, int R = 3>
+__host__ __device__ constexpr size_t smem_euler2d_tma() {
+  return ((smem_euler2d<TX, TY, R>() + 127) & ~size_t(127)) + tma_box_bytes<TX, TY, R>() + 128;
+}
+
+// tm: tensor map of the stage input as [nbatch * 4][ny][nx] doubles, or NULL
+// (plain loads only; the serving engine and tiles of launches without one).
 template <int TX, int TY, bool AI, bool P1, int PREC, int R = 3>
 __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, long long tile,
-                                             bool zeroing_block, double *sm) {
+                                             bool zeroing_block, double *sm,
+                                             const CUtensorMap *tm = nullptr) {
   static_assert(R == 3 || PREC == 0, "FP32 reconstruction is sixth order only");
   constexpr int W = TX + 2 * R, HH = TY + 2 * R, REG = W * HH;
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+  constexpr int XO = TmaBox<R>::XO, BW = TX + 2 * XO;
   double *const pl = sm;
   double *const fx = sm + kPlanes2D * REG;
   double *const fy = fx + NFX * 4;
@@ -211,27 +276,71 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
   const double gm1 = a.gamma - 1.0;
   const int tid = threadIdx.x;
 
+  // TMA staging of an interior tile: the box of the four conserved planes
+  const bool use_tma = tm != nullptr && i0 - XO >= 0 && i0 - XO + BW <= a.nx && j0 - R >= 0 &&
+                       j0 + TY + R <= a.ny;
+  const double *box = reinterpret_cast<const double *>(
+      (reinterpret_cast<uintptr_t>(sm) + ((smem_euler2d<TX, TY, R>() + 127) & ~size_t(127)) + 127) &
+      ~uintptr_t(127));
+  if (use_tma) {
+    __shared__ __align__(8) unsigned long long s_bar;
+    const unsigned bar = smem_u32(&s_bar);
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+      tma_issue_box(tm, bar, const_cast<double *>(box), (int)(i0 - XO), (int)(j0 - R),
+                    (int)(b * 4), (unsigned)tma_box_bytes<TX, TY, R>());
+    long long t_start = clock64();
+    bool done = false;
+    while (!(done = mbar_try_wait(bar, 0)) && clock64() - t_start < kTmaWaitCycles) {
+    }
+    if (!__syncthreads_and(done)) {
+      // The copy did not complete in time: report it (WENO_ERR_TIMEOUT),
+      // give the copy in flight one more bounded wait (it writes into this
+      // block's shared memory), and leave the tile undone.
+      if (tid == 0) record_status(a.status, 5, a.stage, b, j0, i0);
+      t_start = clock64();
+      while (!mbar_try_wait(bar, 0) && clock64() - t_start < kTmaWaitCycles) {
+      }
+      return;
+    }
+  }
+
   // Phase 1: stage the cross-shaped region (tile rows with x halo, tile
   // columns with y halo) and per-cell primitives / fluxes.
   for (int k = tid; k < REG; k += blockDim.x) {
     const int r = k / W, c = k - r * W;
     const bool xb = (r >= R) && (r < R + TY), yb = (c >= R) && (c < R + TX);
     if (!(xb || yb)) continue;
-    const long long gi = ghost(i0 - R + c, a.nx, a.bc_x);
-    const long long jj = j0 - R + r;
-    const double *src = Ub;
-    long long o, pst = plane, gj = jj;
-    if (jj < 0 && a.halo_lo) {  // a neighbour's rows below this strip
-      src = a.halo_lo + b * 4 * (R * a.nx);
-      o = (jj + R) * a.nx + gi;
-      pst = R * a.nx;
-    } else if (jj >= a.ny && a.halo_hi) {  // above it (rows beyond ny+R-1 only
-      src = a.halo_hi + b * 4 * (R * a.nx);  // fill a partial tile: any halo row)
-      o = min(jj - a.ny, (long long)(R - 1)) * a.nx + gi;
-      pst = R * a.nx;
+    const double *src;
+    long long o, pst, gj, gi;
+    if (use_tma) {  // the box: x from i0 - XO, y from j0 - R, planes of problem b
+      src = box;
+      pst = (long long)BW * HH;
+      o = (long long)r * BW + (c + XO - R);
+      gi = i0 - R + c;
+      gj = j0 - R + r;
     } else {
-      gj = ghost(jj, a.ny, a.bc_y);
-      o = gj * a.nx + gi;
+      gi = ghost(i0 - R + c, a.nx, a.bc_x);
+      const long long jj = j0 - R + r;
+      src = Ub;
+      pst = plane;
+      gj = jj;
+      if (jj < 0 && a.halo_lo) {  // a neighbour's rows below this strip
+        src = a.halo_lo + b * 4 * (R * a.nx);
+        o = (jj + R) * a.nx + gi;
+        pst = R * a.nx;
+      } else if (jj >= a.ny && a.halo_hi) {  // above it (rows beyond ny+R-1 only
+        src = a.halo_hi + b * 4 * (R * a.nx);  // fill a partial tile: any halo row)
+        o = min(jj - a.ny, (long long)(R - 1)) * a.nx + gi;
+        pst = R * a.nx;
+      } else {
+        gj = ghost(jj, a.ny, a.bc_y);
+        o = gj * a.nx + gi;
+      }
     }
     const double rho = src[o], mx = src[pst + o], my = src[2 * pst + o], E = src[3 * pst + o];
     const double rs = rsqrt(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
@@ -405,11 +514,14 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
 }
 
 // MINB: resident blocks per SM the register allocation must allow.
+// tm: tensor map of a.Uin (see euler2d_tile), used when a.use_tma is set.
 template <int TX, int TY, int NT, int MINB, bool AI, bool P1, int PREC, int R = 3>
-__global__ void __launch_bounds__(NT, MINB) k_euler2d(const StageArgs a) {
-  extern __shared__ double sm[];
+__global__ void __launch_bounds__(NT, MINB)
+    k_euler2d(const StageArgs a, const __grid_constant__ CUtensorMap tm) {
+  extern __shared__ __align__(128) double sm[];
   euler2d_tile<TX, TY, AI, P1, PREC, R>(a, blockIdx.z, blockIdx.x,
-                                        blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm);
+                                        blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0, sm,
+                                        a.use_tma ? &tm : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -721,15 +833,27 @@ inline int sm_count() {
   return cached[dev];
 }
 
+// Shared memory per SM the resident blocks of a launch may take (228 KB,
+// less 1 KB the hardware keeps per block).
+constexpr size_t kSmemPerSM = 233472;
+
 template <int TX, int TY, int NT, int MINB, bool AI, bool P1, int PREC, int R = 3>
-cudaError_t launch_2d(const StageArgs &a, cudaStream_t s) {
-  const size_t smem = smem_euler2d<TX, TY, R>();
+cudaError_t launch_2d(const StageArgs &a_in, cudaStream_t s) {
+  StageArgs a = a_in;
+  // TMA staging when the box fits beside the tile's planes at this
+  // occupancy and the input is addressable by a tensor map
+  constexpr bool kTmaFits = (smem_euler2d_tma<TX, TY, R>() + 1024) * MINB <= kSmemPerSM;
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  a.use_tma = kTmaFits && encode_state_map(a.Uin, a.nbatch, a.ny, a.nx, TX + 2 * TmaBox<R>::XO,
+                                           TY + 2 * R, &tm);
+  const size_t smem = kTmaFits ? smem_euler2d_tma<TX, TY, R>() : smem_euler2d<TX, TY, R>();
   auto kern = k_euler2d<TX, TY, NT, MINB, AI, P1, PREC, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = ((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
   dim3 grid((unsigned)tiles, 1, (unsigned)a.nbatch);
-  kern<<<grid, NT, smem, s>>>(a);
+  kern<<<grid, NT, smem, s>>>(a, tm);
   return cudaGetLastError();
 }
 
