@@ -254,7 +254,7 @@ WORK_BUDGET = 250e3
 
 
 def serving(n_requests=64, seed=5, loads=(1.0, 1.25), mix="full", policy="two_lane",
-            capacity=False, large_workers=2):
+            capacity=False, large_workers=2, bypass_s=float("inf")):
     """Configuration 5: a seeded Poisson stream of mixed 1D/2D, FP64/FP32-
     reconstruction solves of the configured sizes (2D sides 128..1024, 1D N
     256..16384, 100..1000 steps), n_requests of them (the configured 2000
@@ -281,7 +281,7 @@ def serving(n_requests=64, seed=5, loads=(1.0, 1.25), mix="full", policy="two_la
 
     def run(rs):
         if policy == "two_lane":
-            return serve.serve_two_lane(eng, rs, large_workers=large_workers)
+            return serve.serve_two_lane(eng, rs, large_workers=large_workers, bypass_s=bypass_s)
         return serve.serve_continuous(eng, rs, steps_per_poll=2, work_budget=WORK_BUDGET)
 
     out = {"workload": "%d requests (of the configured 2000; the rest scaled as configured): "
@@ -292,6 +292,8 @@ def serving(n_requests=64, seed=5, loads=(1.0, 1.25), mix="full", policy="two_la
            "policy": policy,
            "large_lane_tiles": serve.full_wave_tiles() if policy == "two_lane" else None,
            "large_lane_workers": large_workers if policy == "two_lane" else None,
+           "bypass_s": (None if bypass_s == float("inf") else bypass_s)
+           if policy == "two_lane" else None,
            "work_budget_cell_units": WORK_BUDGET if policy == "engine" else None,
            "mean_service_s_one_at_a_time": float(np.mean(service)), "loads": []}
     for load in loads:
@@ -484,6 +486,8 @@ def main():
     ap.add_argument("--kernel-tour", action="store_true",
                     help="run each kernel family a few times (for per-kernel ncu captures) and exit")
     ap.add_argument("--serving-large-workers", type=int, default=2)
+    ap.add_argument("--serving-bypass", type=float, default=float("inf"),
+                    help="seconds small solves may overtake the oldest large one (inf: always)")
     ap.add_argument("--serving-capacity", action="store_true",
                     help="also serve every request at t = 0 (one more pass)")
     args = ap.parse_args()
@@ -635,7 +639,8 @@ def main():
         log("serving stream ...")
         result["serving"] = serving(args.serving_requests, mix=args.serving_mix,
                                     policy=args.serving_policy, capacity=args.serving_capacity,
-                                    large_workers=args.serving_large_workers)
+                                    large_workers=args.serving_large_workers,
+                                    bypass_s=args.serving_bypass)
     if rank == 0 and not args.no_cpu_baseline:
         log("timing the CPU oracle on the host cores ...")
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

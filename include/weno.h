@@ -268,6 +268,12 @@ weno_status weno_engine_admit(weno_engine *e, const weno_desc *d, const double *
                               double t_final, int *slot_out);
 /* Enqueue nsteps engine steps (asynchronous). */
 weno_status weno_engine_run(weno_engine *e, int nsteps);
+/* CUDA stream priority of the engine's runs (lower numbers are higher
+ * priorities, clamped to the device's range; the engine starts at the
+ * highest).  run() then launches on a stream of that priority, ordered after
+ * the engine's own stream and before its next poll/admit/retire, so a caller
+ * running other solves beside the engine can let one of them go first. */
+weno_status weno_engine_set_priority(weno_engine *e, int priority);
 /* SSP-RK3 steps per engine step of a fast slot. */
 #define WENO_ENGINE_FAST_STEPS 4
 /* Mark an admitted slot fast (fast = 1: WENO_ENGINE_FAST_STEPS steps per

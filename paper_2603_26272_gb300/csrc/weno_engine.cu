@@ -95,6 +95,11 @@ struct weno_engine {
   std::vector<SlotDev> mirror;
   bool dirty = true;
   long long tiles_in_use = 0;
+  // stream the graphs run on when the caller lowers the engine's priority
+  // (weno_engine_set_priority); events keep it in order with `s`
+  cudaStream_t s_run = nullptr;
+  int run_priority = 0, greatest_priority = 0;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t graph = nullptr;       // one sub-step per engine step
   cudaGraphExec_t graph_fast = nullptr;  // WENO_ENGINE_FAST_STEPS sub-steps
   int n_fast = 0;                        // used slots marked fast
@@ -255,6 +260,7 @@ weno_status weno_engine_create(void *arena, size_t arena_bytes, int max_slots, i
   int prio_least = 0, prio_greatest = 0;
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&E->s, cudaStreamNonBlocking, prio_greatest);
+  E->run_priority = E->greatest_priority = prio_greatest;
   if (e != cudaSuccess) {
     delete E;
     return ecuda(e, "cudaStreamCreateWithFlags");
@@ -395,10 +401,50 @@ weno_status weno_engine_run(weno_engine *E, int nsteps) {
     if (st != WENO_OK) return st;
   }
   cudaGraphExec_t g = E->n_fast > 0 ? E->graph_fast : E->graph;
+  cudaStream_t rs = E->s_run ? E->s_run : E->s;
+  cudaError_t e = cudaSuccess;
+  if (rs != E->s) {  // the run stream starts after everything enqueued on s
+    e = cudaEventRecord(E->ev_in, E->s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, E->ev_in, 0);
+    if (e != cudaSuccess) return ecuda(e, "engine stream order");
+  }
   for (int q = 0; q < nsteps; ++q) {
-    cudaError_t e = cudaGraphLaunch(g, E->s);
+    e = cudaGraphLaunch(g, rs);
     if (e != cudaSuccess) return ecuda(e, "cudaGraphLaunch");
   }
+  if (rs != E->s) {  // and s (polls, admissions) after the run
+    e = cudaEventRecord(E->ev_out, rs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(E->s, E->ev_out, 0);
+    if (e != cudaSuccess) return ecuda(e, "engine stream order");
+  }
+  return WENO_OK;
+}
+
+weno_status weno_engine_set_priority(weno_engine *E, int priority) {
+  if (!E) return efail(WENO_ERR_ARG, "NULL engine");
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e != cudaSuccess) return ecuda(e, "cudaDeviceGetStreamPriorityRange");
+  if (priority < greatest) priority = greatest;  // lower numbers are higher priorities
+  if (priority > least) priority = least;
+  if (priority == E->run_priority) return WENO_OK;
+  cudaStream_t ns = nullptr;
+  if (priority != E->greatest_priority) {
+    e = cudaStreamCreateWithPriority(&ns, cudaStreamNonBlocking, priority);
+    if (e == cudaSuccess && !E->ev_in) e = cudaEventCreateWithFlags(&E->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess && !E->ev_out)
+      e = cudaEventCreateWithFlags(&E->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (ns) cudaStreamDestroy(ns);
+      return ecuda(e, "engine run stream");
+    }
+  }
+  if (E->s_run) {  // the old run stream's work is ordered before s already
+    cudaStreamSynchronize(E->s_run);
+    cudaStreamDestroy(E->s_run);
+  }
+  E->s_run = ns;
+  E->run_priority = priority;
   return WENO_OK;
 }
 
@@ -488,6 +534,12 @@ weno_status weno_engine_info(const weno_engine *E, size_t *heap_free_bytes, size
 weno_status weno_engine_destroy(weno_engine *E) {
   if (!E) return WENO_OK;
   cudaStreamSynchronize(E->s);
+  if (E->s_run) {
+    cudaStreamSynchronize(E->s_run);
+    cudaStreamDestroy(E->s_run);
+  }
+  if (E->ev_in) cudaEventDestroy(E->ev_in);
+  if (E->ev_out) cudaEventDestroy(E->ev_out);
   if (E->graph) cudaGraphExecDestroy(E->graph);
   if (E->graph_fast) cudaGraphExecDestroy(E->graph_fast);
   if (E->own_stream) cudaStreamDestroy(E->s);

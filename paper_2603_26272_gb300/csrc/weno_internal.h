@@ -56,8 +56,10 @@ struct StageArgs {
   const double *halo_lo, *halo_hi;
   double *send_lo, *send_hi;
   // set by the 2D launcher: interior tiles stage by TMA through the tensor
-  // map passed beside these arguments
-  int use_tma;
+  // map passed beside these arguments; tma_no_copy (a test of the bounded
+  // wait, WENO_TEST_TMA_NO_COPY=1 in the environment) arms the barrier but
+  // issues no copy, so every TMA wait runs out and reports WENO_ERR_TIMEOUT
+  int use_tma, tma_no_copy;
 };
 
 // Wavespeed reduction of U into alpha_out (which must be zero), optional dt.

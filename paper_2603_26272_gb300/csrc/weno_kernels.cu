@@ -146,7 +146,7 @@ __device__ __forceinline__ StageArgs slot_stage_args(const SlotDev &S, int stage
   a.t_final = S.t_final;
   a.halo_lo = a.halo_hi = nullptr;
   a.send_lo = a.send_hi = nullptr;
-  a.use_tma = 0;
+  a.use_tma = a.tma_no_copy = 0;
   a.t = S.clock;
   a.tnext = S.clock + 1;
   a.dt = S.clock + 2;

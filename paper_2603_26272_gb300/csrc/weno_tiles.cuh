@@ -24,6 +24,7 @@
 #pragma once
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include <cuda.h>  // CUtensorMap (the type only; the encoder is fetched at run time)
@@ -290,9 +291,15 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0)
-      tma_issue_box(tm, bar, const_cast<double *>(box), (int)(i0 - XO), (int)(j0 - R),
-                    (int)(b * 4), (unsigned)tma_box_bytes<TX, TY, R>());
+    if (tid == 0) {
+      if (a.tma_no_copy)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((unsigned)tma_box_bytes<TX, TY, R>())
+                     : "memory");
+      else
+        tma_issue_box(tm, bar, const_cast<double *>(box), (int)(i0 - XO), (int)(j0 - R),
+                      (int)(b * 4), (unsigned)tma_box_bytes<TX, TY, R>());
+    }
     long long t_start = clock64();
     bool done = false;
     while (!(done = mbar_try_wait(bar, 0)) && clock64() - t_start < kTmaWaitCycles) {
@@ -847,6 +854,8 @@ cudaError_t launch_2d(const StageArgs &a_in, cudaStream_t s) {
   std::memset(&tm, 0, sizeof(tm));
   a.use_tma = kTmaFits && encode_state_map(a.Uin, a.nbatch, a.ny, a.nx, TX + 2 * TmaBox<R>::XO,
                                            TY + 2 * R, &tm);
+  const char *nc = std::getenv("WENO_TEST_TMA_NO_COPY");
+  a.tma_no_copy = (nc && nc[0] == '1') ? 1 : 0;
   const size_t smem = kTmaFits ? smem_euler2d_tma<TX, TY, R>() : smem_euler2d<TX, TY, R>();
   auto kern = k_euler2d<TX, TY, NT, MINB, AI, P1, PREC, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -44,6 +44,8 @@ class _EngineLib:
                                         ctypes.c_double, P(ctypes.c_int)]
         L.weno_engine_run.restype = ctypes.c_int
         L.weno_engine_run.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.weno_engine_set_priority.restype = ctypes.c_int
+        L.weno_engine_set_priority.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.weno_engine_set_fast.restype = ctypes.c_int
         L.weno_engine_set_fast.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.weno_engine_poll.restype = ctypes.c_int
@@ -110,6 +112,10 @@ class Engine:
 
     def run(self, nsteps):
         weno._check(_lib().weno_engine_run(self.h, int(nsteps)))
+
+    def set_priority(self, priority):
+        """CUDA stream priority of the engine's runs (lower = higher)."""
+        weno._check(_lib().weno_engine_set_priority(self.h, int(priority)))
 
     def set_fast(self, slot, fast=True):
         """Fast slots take FAST_STEPS SSP-RK3 steps per engine step."""
@@ -315,7 +321,8 @@ def full_wave_tiles(device=None):
 
 
 def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_per_poll=2,
-                   keep_states=False, chunk_steps=16, clock=time.perf_counter):
+                   keep_states=False, chunk_steps=16, bypass_s=float("inf"),
+                   clock=time.perf_counter):
     """Continuous batching with a lane for the solves that fill the GPU alone.
 
     A 2D solve of at least `large_tiles` tiles (default: one full wave of
@@ -337,6 +344,14 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
     large one, and the GPU time a small solve alone would leave idle (a
     latency-bound stage on a few SMs) goes to the large solve.
 
+    `bypass_s` bounds how far small solves may overtake a large one: while
+    the engine's oldest solve arrived more than bypass_s after the oldest
+    large solve in progress, the engine runs at a priority between the
+    oldest large solve's and the younger ones' (the oldest large solve goes
+    first, the engine fills what it leaves).  0 keeps arrival order between
+    the lanes (every solve then finishes about as it would one at a time,
+    or sooner); infinity lets small solves always go first.
+
     Fills request.result like serve_continuous (plus "lane")."""
     import queue
     import threading
@@ -352,21 +367,32 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
     errors = []
 
     order = []  # large solves in progress, oldest first
+    arrival_of = {}
     lock = threading.Lock()
+    # stream priorities (lower = higher): engine first by default, then the
+    # oldest large solve, then the engine when it must yield, then the
+    # younger large solves
+    least, greatest = torch.cuda.Stream.priority_range()
+    clamp = lambda q: min(max(q, greatest), least)  # noqa: E731
+    prio_engine_hi, prio_large_old = greatest, clamp(greatest + 1)
+    prio_engine_lo, prio_large_young = clamp(greatest + 2), least
+    engine.set_priority(prio_engine_hi)
+    engine_prio = prio_engine_hi
 
     def big_lane():
         torch.cuda.set_device(device)
-        # the oldest large solve on a stream above the others (still below
-        # the engine's), so it keeps the pace it has alone and the younger
-        # ones take only the places its blocks leave free
-        s_old = torch.cuda.Stream(device=device, priority=-1)
-        s_new = torch.cuda.Stream(device=device, priority=0)
+        # the oldest large solve on a stream above the others (below the
+        # engine's while it has priority), so it keeps the pace it has alone
+        # and the younger ones take only the places its blocks leave free
+        s_old = torch.cuda.Stream(device=device, priority=prio_large_old)
+        s_new = torch.cuda.Stream(device=device, priority=prio_large_young)
         while True:
             r = big_q.get()
             if r is None:
                 return
             with lock:
                 order.append(r.rid)
+                arrival_of[r.rid] = r.arrival
             try:
                 with torch.cuda.stream(s_new):
                     U = torch.from_numpy(r.U).to(device)
@@ -425,6 +451,16 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
                 raise RuntimeError("request %d does not fit the empty engine (arena or work list "
                                    "too small)" % waiting[0].rid)
             if active:
+                want = prio_engine_hi
+                with lock:
+                    if order:
+                        oldest_large = arrival_of[order[0]]
+                        oldest_small = min(r.arrival for r in active.values())
+                        if oldest_small > oldest_large + bypass_s:
+                            want = prio_engine_lo
+                if want != engine_prio:
+                    engine.set_priority(want)
+                    engine_prio = want
                 engine.run(steps_per_poll)
                 done, _ = engine.poll()
                 for slot in done:
@@ -440,6 +476,7 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
             big_q.put(None)
         for wk in workers:
             wk.join()
+        engine.set_priority(prio_engine_hi)
     if errors:
         raise errors[0]
     for r in requests:

@@ -330,11 +330,15 @@ def test_config3_step_count_near_table7():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_recon"])
-def test_tile_variants_are_bitwise_identical(prec, monkeypatch):
+@pytest.mark.parametrize("nx,ny", [(75, 53), (96, 70)])
+def test_tile_variants_are_bitwise_identical(prec, nx, ny, monkeypatch):
     """The autotuner may pick any 2D tile shape; every face is computed with
-    the same arithmetic, so the shapes must agree bit for bit (ragged grid)."""
-    w = wl.quadrant_2d(n=75, seed=6)
-    w["U"] = np.ascontiguousarray(w["U"][:, :, :53, :])
+    the same arithmetic, so the shapes must agree bit for bit (ragged grids).
+    On the even-width grid the interior tiles of seven variants stage by TMA
+    while 16x8 with 6 blocks per SM and 26x14 (no shared memory to spare) and
+    all boundary tiles use plain loads: the two ways of staging agree too."""
+    w = wl.quadrant_2d(n=max(nx, ny), seed=6)
+    w["U"] = np.ascontiguousarray(w["U"][:, :, :ny, :nx])
     d = _fix_2d_domain(w, weno.desc_for(w, precision=prec))
     outs = []
     for v in ("0", "1", "2", "3", "4", "5", "6", "7", "8"):
@@ -350,6 +354,30 @@ def test_tile_variants_are_bitwise_identical(prec, monkeypatch):
     for _ in range(3):
         weno.step(d, U)
     assert np.array_equal(U.cpu().numpy(), outs[0])
+
+
+def test_tma_wait_is_bounded_and_reported(monkeypatch):
+    """The TMA staging waits for its copy with a bound on the SM clock.  With
+    WENO_TEST_TMA_NO_COPY=1 the kernels arm the barrier but issue no copy (a
+    flag nothing else sets), so each interior tile's wait runs out: the call
+    reports WENO_ERR_TIMEOUT instead of hanging, and the context stays usable
+    -- the next call without the switch matches the oracle."""
+    w = wl.quadrant_2d(n=64, seed=8)
+    w["U"] = np.ascontiguousarray(w["U"][:, :, :40, :])
+    d = _fix_2d_domain(w, weno.desc_for(w))
+    monkeypatch.setenv("WENO_TILE2D", "3")
+    monkeypatch.setenv("WENO_TEST_TMA_NO_COPY", "1")
+    Ug = to_gpu(w["U"])
+    ws = weno.workspace(d)
+    weno.rhs(d, Ug, ws=ws)
+    with pytest.raises(weno.WenoError) as ei:
+        weno.sync_status(d, ws)
+    assert ei.value.code == weno.WENO_ERR_TIMEOUT
+    monkeypatch.delenv("WENO_TEST_TMA_NO_COPY")
+    L = weno.rhs(d, Ug, ws=ws).cpu().numpy()
+    weno.sync_status(d, ws)
+    g = ora_grid(w, d)
+    assert rel_err(L, oracle.rhs(g, w["U"])) <= STAGE_TOL
 
 
 def test_advection_sixth_order_on_gpu():

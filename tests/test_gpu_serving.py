@@ -44,16 +44,18 @@ def test_alone_equals_in_the_mix():
     eng.close()
 
 
-def test_two_lane_results_equal_alone():
+@pytest.mark.parametrize("bypass", [float("inf"), 0.0])
+def test_two_lane_results_equal_alone(bypass):
     """The serving loop's two lanes: solves that fill a full wave of tiles run
     one at a time on a low-priority stream (here: the 2D side-400 requests,
     large_tiles lowered to 600), the others through the high-priority
-    engine; every result is bitwise the solve alone, and both lanes are used
-    while requests arrive over time."""
+    engine -- or, with bypass 0, below the oldest large solve, the engine's
+    runs switching streams; every result is bitwise the solve alone, and
+    both lanes are used while requests arrive over time."""
     reqs = serve.make_requests(12, seed=25, rate=40.0, sides_2d=(40, 64, 400), n1d=(60, 3000),
                                steps=(15, 40))
     eng = serve.Engine(arena_bytes=512 << 20, max_slots=32)
-    serve.serve_two_lane(eng, reqs, large_tiles=600, keep_states=True)
+    serve.serve_two_lane(eng, reqs, large_tiles=600, keep_states=True, bypass_s=bypass)
     lanes = set()
     for r in reqs:
         U, t, n = _alone(r)
