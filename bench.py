@@ -254,7 +254,7 @@ WORK_BUDGET = 250e3
 
 
 def serving(n_requests=64, seed=5, loads=(1.0, 1.25), mix="full", policy="two_lane",
-            capacity=False, large_workers=2, bypass_s=float("inf")):
+            capacity=False, large_workers=2, bypass_s=0.0):
     """Configuration 5: a seeded Poisson stream of mixed 1D/2D, FP64/FP32-
     reconstruction solves of the configured sizes (2D sides 128..1024, 1D N
     256..16384, 100..1000 steps), n_requests of them (the configured 2000
@@ -486,8 +486,9 @@ def main():
     ap.add_argument("--kernel-tour", action="store_true",
                     help="run each kernel family a few times (for per-kernel ncu captures) and exit")
     ap.add_argument("--serving-large-workers", type=int, default=2)
-    ap.add_argument("--serving-bypass", type=float, default=float("inf"),
-                    help="seconds small solves may overtake the oldest large one (inf: always)")
+    ap.add_argument("--serving-bypass", type=float, default=0.0,
+                    help="seconds small solves may overtake the oldest large one (0: arrival "
+                         "order between the lanes; inf: small solves always first)")
     ap.add_argument("--serving-capacity", action="store_true",
                     help="also serve every request at t = 0 (one more pass)")
     args = ap.parse_args()

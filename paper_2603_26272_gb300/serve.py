@@ -321,7 +321,7 @@ def full_wave_tiles(device=None):
 
 
 def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_per_poll=2,
-                   keep_states=False, chunk_steps=16, bypass_s=float("inf"),
+                   keep_states=False, chunk_steps=16, bypass_s=0.0,
                    clock=time.perf_counter):
     """Continuous batching with a lane for the solves that fill the GPU alone.
 
