@@ -627,6 +627,9 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
+    if world > 1:  # the extra sections are single-GPU lines; don't hold N GPUs for them
+        args.no_precision_modes = args.no_orders = args.no_serving = True
+        args.no_cpu_baseline = True
     if not args.no_precision_modes:
         del U
         torch.cuda.empty_cache()

@@ -96,8 +96,10 @@ struct weno_engine {
   bool dirty = true;
   long long tiles_in_use = 0;
   // stream the graphs run on when the caller lowers the engine's priority
-  // (weno_engine_set_priority); events keep it in order with `s`
+  // (weno_engine_set_priority; one stream per priority used, kept until
+  // destroy); events keep it in order with `s`
   cudaStream_t s_run = nullptr;
+  std::map<int, cudaStream_t> run_streams;
   int run_priority = 0, greatest_priority = 0;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t graph = nullptr;       // one sub-step per engine step
@@ -428,21 +430,26 @@ weno_status weno_engine_set_priority(weno_engine *E, int priority) {
   if (priority < greatest) priority = greatest;  // lower numbers are higher priorities
   if (priority > least) priority = least;
   if (priority == E->run_priority) return WENO_OK;
-  cudaStream_t ns = nullptr;
+  cudaStream_t ns = nullptr;  // NULL: the engine's own stream (the highest priority)
   if (priority != E->greatest_priority) {
-    e = cudaStreamCreateWithPriority(&ns, cudaStreamNonBlocking, priority);
-    if (e == cudaSuccess && !E->ev_in) e = cudaEventCreateWithFlags(&E->ev_in, cudaEventDisableTiming);
-    if (e == cudaSuccess && !E->ev_out)
-      e = cudaEventCreateWithFlags(&E->ev_out, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-      if (ns) cudaStreamDestroy(ns);
-      return ecuda(e, "engine run stream");
+    auto it = E->run_streams.find(priority);
+    if (it != E->run_streams.end()) {
+      ns = it->second;
+    } else {
+      e = cudaStreamCreateWithPriority(&ns, cudaStreamNonBlocking, priority);
+      if (e == cudaSuccess && !E->ev_in)
+        e = cudaEventCreateWithFlags(&E->ev_in, cudaEventDisableTiming);
+      if (e == cudaSuccess && !E->ev_out)
+        e = cudaEventCreateWithFlags(&E->ev_out, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        if (ns) cudaStreamDestroy(ns);
+        return ecuda(e, "engine run stream");
+      }
+      E->run_streams[priority] = ns;
     }
   }
-  if (E->s_run) {  // the old run stream's work is ordered before s already
-    cudaStreamSynchronize(E->s_run);
-    cudaStreamDestroy(E->s_run);
-  }
+  // every run on the previous stream is ordered before `s` (run() makes `s`
+  // wait for it), and the next run waits for `s`: switching needs no sync
   E->s_run = ns;
   E->run_priority = priority;
   return WENO_OK;
@@ -534,9 +541,9 @@ weno_status weno_engine_info(const weno_engine *E, size_t *heap_free_bytes, size
 weno_status weno_engine_destroy(weno_engine *E) {
   if (!E) return WENO_OK;
   cudaStreamSynchronize(E->s);
-  if (E->s_run) {
-    cudaStreamSynchronize(E->s_run);
-    cudaStreamDestroy(E->s_run);
+  for (auto &kv : E->run_streams) {
+    cudaStreamSynchronize(kv.second);
+    cudaStreamDestroy(kv.second);
   }
   if (E->ev_in) cudaEventDestroy(E->ev_in);
   if (E->ev_out) cudaEventDestroy(E->ev_out);
