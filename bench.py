@@ -485,6 +485,8 @@ def main():
     ap.add_argument("--serving-policy", choices=["two_lane", "engine"], default="two_lane")
     ap.add_argument("--kernel-tour", action="store_true",
                     help="run each kernel family a few times (for per-kernel ncu captures) and exit")
+    ap.add_argument("--serving-loads", type=float, nargs="+", default=[1.0, 1.25],
+                    help="offered loads, as multiples of the one-at-a-time capacity")
     ap.add_argument("--serving-large-workers", type=int, default=2)
     ap.add_argument("--serving-bypass", type=float, default=0.0,
                     help="seconds small solves may overtake the oldest large one (0: arrival "
@@ -641,7 +643,8 @@ def main():
         result["gpu_launches_scheme_orders"] = 4 * 4 * (4 + 3)
     if not args.no_serving and rank == 0:
         log("serving stream ...")
-        result["serving"] = serving(args.serving_requests, mix=args.serving_mix,
+        result["serving"] = serving(args.serving_requests, loads=tuple(args.serving_loads),
+                                    mix=args.serving_mix,
                                     policy=args.serving_policy, capacity=args.serving_capacity,
                                     large_workers=args.serving_large_workers,
                                     bypass_s=args.serving_bypass)
