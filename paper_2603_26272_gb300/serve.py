@@ -320,9 +320,63 @@ def full_wave_tiles(device=None):
     return 3 * torch.cuda.get_device_properties(device or torch.cuda.current_device()).multi_processor_count
 
 
+class GpuLargeRunner:
+    """Runs one large solve of the two-lane loop on the GPU: the state goes to
+    the device, and weno_solve advances it in chunks of `chunk_steps` steps
+    from the time reached (bitwise one call), each chunk on the stream of the
+    oldest large solve or on the younger ones' stream, as `is_oldest()` says
+    when the chunk starts.  One runner per worker thread."""
+
+    def __init__(self, device, prio_oldest, prio_younger, chunk_steps=16, keep_states=False):
+        torch.cuda.set_device(device)
+        self.device = device
+        self.s_old = torch.cuda.Stream(device=device, priority=prio_oldest)
+        self.s_new = torch.cuda.Stream(device=device, priority=prio_younger)
+        self.chunk = chunk_steps
+        self.keep = keep_states
+
+    def upload(self, r):
+        with torch.cuda.stream(self.s_new):
+            U = torch.from_numpy(r.U).to(self.device)
+            ws = weno.workspace(r.desc, device=self.device)
+        self.s_new.synchronize()
+        return U, ws
+
+    def run(self, r, state, is_oldest):
+        """Returns (t reached, steps, status code, final state or None)."""
+        U, ws = state
+        t, steps, status = 0.0, 0, 0
+        while t < r.t_final:
+            st = self.s_old if is_oldest() else self.s_new
+            try:
+                tt, nn = weno.solve(r.desc, U, r.t_final, t0=t, max_steps=self.chunk, ws=ws,
+                                    stream=st, allow_max_steps=True)
+            except weno.WenoError as e:
+                status = e.code
+                break
+            t, steps = tt[0], steps + nn[0]
+            if nn[0] == 0:
+                break
+        return (t if status == 0 else float("nan")), steps, status, \
+            (U.cpu().numpy() if self.keep else None)
+
+
+def stream_priority_levels():
+    """CUDA stream priorities of the two-lane loop (lower = higher): the
+    engine when it goes first, the oldest large solve, the engine when it
+    yields, the younger large solves."""
+    least, greatest = torch.cuda.Stream.priority_range()
+
+    def clamp(q):
+        return min(max(q, greatest), least)
+
+    return {"engine_first": greatest, "large_oldest": clamp(greatest + 1),
+            "engine_yields": clamp(greatest + 2), "large_younger": least}
+
+
 def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_per_poll=2,
-                   keep_states=False, chunk_steps=16, bypass_s=0.0,
-                   clock=time.perf_counter):
+                   keep_states=False, chunk_steps=16, bypass_s=0.0, priorities=None,
+                   large_runner=None, clock=time.perf_counter):
     """Continuous batching with a lane for the solves that fill the GPU alone.
 
     A 2D solve of at least `large_tiles` tiles (default: one full wave of
@@ -336,13 +390,13 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
     than the younger ones (each solve goes in chunks of `chunk_steps` steps,
     weno_solve from the reached time, bitwise one call, and picks its stream
     per chunk), so it keeps the pace it has alone and first come first served
-    holds for the large solves.  Every other solve (1D, small
-    2D) is admitted to the engine as soon as it arrives and there is room;
-    the engine's stream has the highest priority, so its blocks take the
-    places the large solve's blocks free and the small solves keep roughly
-    the pace they have alone.  A small solve therefore never waits for a
-    large one, and the GPU time a small solve alone would leave idle (a
-    latency-bound stage on a few SMs) goes to the large solve.
+    holds for the large solves.  Every other solve (1D, small 2D) is
+    admitted to the engine as soon as it arrives and there is room; the
+    engine's stream has the highest priority, so its blocks take the places
+    the large solve's blocks free and the small solves keep roughly the pace
+    they have alone.  A small solve therefore never waits for a large one,
+    and the GPU time a small solve alone would leave idle (a latency-bound
+    stage on a few SMs) goes to the large solve.
 
     `bypass_s` bounds how far small solves may overtake a large one: while
     the engine's oldest solve arrived more than bypass_s after the oldest
@@ -352,40 +406,37 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
     the lanes (every solve then finishes about as it would one at a time,
     or sooner); infinity lets small solves always go first.
 
+    `priorities` (default stream_priority_levels()) and `large_runner` (a
+    factory called once per worker thread; default: a GpuLargeRunner) are
+    parameters so the host logic can run without a GPU.
+
     Fills request.result like serve_continuous (plus "lane")."""
     import queue
     import threading
 
     if large_tiles is None:
         large_tiles = full_wave_tiles()
+    pr = priorities or stream_priority_levels()
+    if large_runner is None:
+        device = torch.cuda.current_device()
+
+        def large_runner():
+            return GpuLargeRunner(device, pr["large_oldest"], pr["large_younger"], chunk_steps,
+                                  keep_states)
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     waiting = []
     active = {}
     big_q = queue.Queue()
     t0 = clock()
-    device = torch.cuda.current_device()
     errors = []
-
     order = []  # large solves in progress, oldest first
     arrival_of = {}
     lock = threading.Lock()
-    # stream priorities (lower = higher): engine first by default, then the
-    # oldest large solve, then the engine when it must yield, then the
-    # younger large solves
-    least, greatest = torch.cuda.Stream.priority_range()
-    clamp = lambda q: min(max(q, greatest), least)  # noqa: E731
-    prio_engine_hi, prio_large_old = greatest, clamp(greatest + 1)
-    prio_engine_lo, prio_large_young = clamp(greatest + 2), least
-    engine.set_priority(prio_engine_hi)
-    engine_prio = prio_engine_hi
+    engine.set_priority(pr["engine_first"])
+    engine_prio = pr["engine_first"]
 
     def big_lane():
-        torch.cuda.set_device(device)
-        # the oldest large solve on a stream above the others (below the
-        # engine's while it has priority), so it keeps the pace it has alone
-        # and the younger ones take only the places its blocks leave free
-        s_old = torch.cuda.Stream(device=device, priority=prio_large_old)
-        s_new = torch.cuda.Stream(device=device, priority=prio_large_young)
+        runner = large_runner()
         while True:
             r = big_q.get()
             if r is None:
@@ -394,28 +445,17 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
                 order.append(r.rid)
                 arrival_of[r.rid] = r.arrival
             try:
-                with torch.cuda.stream(s_new):
-                    U = torch.from_numpy(r.U).to(device)
-                    ws = weno.workspace(r.desc, device=device)
-                s_new.synchronize()
+                state = runner.upload(r)
                 r.result["admit"] = clock() - t0
-                t, steps, status = 0.0, 0, 0
-                while t < r.t_final:
+
+                def is_oldest(rid=r.rid):
                     with lock:
-                        st = s_old if order[0] == r.rid else s_new
-                    try:
-                        tt, nn = weno.solve(r.desc, U, r.t_final, t0=t, max_steps=chunk_steps,
-                                            ws=ws, stream=st, allow_max_steps=True)
-                    except weno.WenoError as e:
-                        status = e.code
-                        break
-                    t, steps = tt[0], steps + nn[0]
-                    if nn[0] == 0:
-                        break
-                r.result.update({"t": t if status == 0 else float("nan"), "steps": steps,
-                                 "status": status})
-                if keep_states:
-                    r.result["U"] = U.cpu().numpy()
+                        return order[0] == rid
+
+                t, steps, status, U = runner.run(r, state, is_oldest)
+                r.result.update({"t": t, "steps": steps, "status": status})
+                if U is not None:
+                    r.result["U"] = U
                 r.result["done"] = clock() - t0
             except Exception as e:  # noqa: BLE001 -- reported by the main thread
                 errors.append(e)
@@ -451,13 +491,13 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
                 raise RuntimeError("request %d does not fit the empty engine (arena or work list "
                                    "too small)" % waiting[0].rid)
             if active:
-                want = prio_engine_hi
+                want = pr["engine_first"]
                 with lock:
                     if order:
                         oldest_large = arrival_of[order[0]]
                         oldest_small = min(r.arrival for r in active.values())
                         if oldest_small > oldest_large + bypass_s:
-                            want = prio_engine_lo
+                            want = pr["engine_yields"]
                 if want != engine_prio:
                     engine.set_priority(want)
                     engine_prio = want
@@ -476,7 +516,7 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
             big_q.put(None)
         for wk in workers:
             wk.join()
-        engine.set_priority(prio_engine_hi)
+        engine.set_priority(pr["engine_first"])
     if errors:
         raise errors[0]
     for r in requests:
