@@ -583,7 +583,7 @@ def main():
     flops = cells * FLOPS_PER_CELL_STAGE
     achieved = flops / (stage_ms / 1e3) / 1e12
     rec = ncu_record()
-    traffic = rec.get("dram_bytes_per_launch_2048")
+    traffic = rec.get("dram_bytes_per_launch_2048") if n == 2048 else None
     clocks_peak = Clocks(gpu_id)
     clocks_peak.start()
     peaks = fma_peaks(weno)
@@ -610,12 +610,18 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
     }
     fp64_ops = rec.get("fp64_flops_per_launch_2048")
-    if fp64_ops:
+    if fp64_ops and n == 2048:
         ex = fp64_ops / (stage_ms / 1e3) / 1e12
+        instr = sum(rec.get("fp64_instructions_per_launch_2048", {}).values())
         roofline["executed"] = {"fp64_flops_per_launch": fp64_ops, "achieved": ex,
                                 "frac": ex / fp64_peak,
                                 "source": "ncu sm__sass_thread_inst_executed_op_d{fma,add,mul}"
                                           "_pred_on (fma = 2) of one launch, profiles/"}
+        if instr:
+            # every FP64 instruction takes one issue slot of the pipe, whatever
+            # its flops: its rate against the measured FMA instruction rate
+            roofline["executed"]["fp64_instructions_per_launch"] = instr
+            roofline["executed"]["issue_frac"] = (instr / (stage_ms / 1e3)) / (fp64_peak * 1e12 / 2)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
