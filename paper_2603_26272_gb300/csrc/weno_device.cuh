@@ -30,7 +30,73 @@ struct ReconParams {
   double p;      // power parameter of eq. (21)
   double me;     // sqrt(4 eps) / 6    (Ai: 4 eps mu^2 = (me * dev + mo)^2, dev =
   double mo;     // sqrt(4 eps) * scale * mu_0   the sum of |v_j - mean v|)
+  double e0;     // mo^2: the term of a flat stencil (dev = 0)
+  float mef;     // me^2 = eps / 9 = mef 2^eme, mef in [1, 2) (FP32)
+  int eme;
+  int lthr;      // dev >= 2^(lthr - 1019) implies me dev >= 2^30 mo (mo negligible)
 };
+
+// ---------------------------------------------------------------------------
+// Format changes on the integer pipe.  An FP64 <-> FP32 conversion issues to
+// the FP64 pipe, the one these kernels are bound by; where a value only needs
+// FP32 accuracy the helpers below move between the formats with integer
+// instructions on the bit patterns instead.
+// ---------------------------------------------------------------------------
+
+// x 2^(1019 - es) as FP32 with the mantissa truncated to 23 bits, where es is
+// at least the biased exponent of x (so the result is below 2^-3 in
+// magnitude); 0 where the result would fall below FP32's normal range.
+__device__ __forceinline__ float f32_scaled(double x, int es) {
+  const int hi = __double2hiint(x);
+  const int fe = ((hi >> 20) & 0x7FF) - es + 123;
+  const unsigned m = __funnelshift_r((unsigned)__double2loint(x), (unsigned)hi, 29) & 0x7FFFFFu;
+  const unsigned b = ((unsigned)hi & 0x80000000u) | ((unsigned)fe << 23) | m;
+  return (fe > 0 && (hi & 0x7FF00000) != 0) ? __uint_as_float(b) : 0.0f;
+}
+
+// x 2^(1019 - es) rounded to FP32 (to nearest, ties away from zero), with es
+// at least the biased exponent of x; 0 below FP32's normal range.
+__device__ __forceinline__ float f32_scaled_rn(double x, int es) {
+  const unsigned lo = (unsigned)__double2loint(x), lor = lo + 0x10000000u;
+  const int hi = __double2hiint(x) + (lor < lo ? 1 : 0);  // a carry into the exponent is exact
+  const int fe = ((hi >> 20) & 0x7FF) - es + 123;
+  const unsigned m = __funnelshift_r(lor, (unsigned)hi, 29) & 0x7FFFFFu;
+  const unsigned b = ((unsigned)hi & 0x80000000u) | ((unsigned)fe << 23) | m;
+  return (fe > 0 && (__double2hiint(x) & 0x7FF00000) != 0) ? __uint_as_float(b) : 0.0f;
+}
+
+// x rounded to FP32 (to nearest, ties away from zero): 0 below FP32's normal
+// range, infinite above it.
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned lo = (unsigned)__double2loint(x), lor = lo + 0x10000000u;
+  const int hi = __double2hiint(x) + (lor < lo ? 1 : 0);
+  const int fe = ((hi >> 20) & 0x7FF) - 896;
+  const unsigned sg = (unsigned)hi & 0x80000000u;
+  const unsigned m = __funnelshift_r(lor, (unsigned)hi, 29) & 0x7FFFFFu;
+  const unsigned b = fe <= 0 ? sg : (fe >= 255 ? (sg | 0x7F800000u) : (sg | ((unsigned)fe << 23) | m));
+  return __uint_as_float(b);
+}
+
+// y 2^k as FP64 for any FP32 y: exact for a normal y whose image is a normal
+// double; 0 for a zero or subnormal y or below FP64's normal range; infinite
+// above it (and for an infinite or NaN y).
+__device__ __forceinline__ double f64_of_f32(float y, int k) {
+  const unsigned b = __float_as_uint(y), sg = b & 0x80000000u;
+  const int fe = (int)((b >> 23) & 0xFFu);
+  const int F = fe + 896 + k;
+  const unsigned hi = (fe == 0 || F <= 0)  ? sg
+                      : (fe == 255 || F >= 2047) ? (sg | 0x7FF00000u)
+                      : (sg | ((unsigned)(F << 20) + ((b >> 3) & 0xFFFFFu)));
+  const unsigned lo = (fe == 0 || F <= 0 || fe == 255 || F >= 2047) ? 0u : (b << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// y 2^k as FP64 for a positive normal FP32 y, exactly (the caller keeps the
+// result inside FP64's normal range).
+__device__ __forceinline__ double f64_of_f32_pos(float y, int k) {
+  const unsigned b = __float_as_uint(y);
+  return __hiloint2double((int)(b >> 3) + ((896 + k) << 20), (int)(b << 29));
+}
 
 // f > 0 and finite, by the bit pattern (integer pipe only).
 __device__ __forceinline__ bool pos_finite(double x) {
@@ -91,21 +157,22 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 // weights, the weight denominators, 1/rho), by Newton-Raphson.  With
 // x = m 2^E, m in [1, 2), the seed is the FP32 approximate reciprocal of m
 // (rcp.approx.ftz.f32 on the special-function unit, within about 2^-22
-// of 1/m after the rounding of m to FP32) scaled by 2^-E on the integer pipe;
-// one cubic Newton-Raphson step, r <- r + r (e + e^2) with e = 1 - x r,
-// leaves a relative error of about e^3 < 2^-66, so the result is 1/x to
-// within the FP64 rounding of its three fused multiply-adds (about 1 ulp).
-// Three FP64 operations instead of the ~8 pipe slots of an IEEE division.
-// (Inputs outside the positive normal range -- a nonphysical state, which
-// the kernels report separately -- give a meaningless but finite value.)
+// of 1/m after m is truncated to FP32's 23 mantissa bits), made an FP64
+// number scaled by 2^-E on the integer pipe; one cubic Newton-Raphson step,
+// r <- r + r (e + e^2) with e = 1 - x r, leaves a relative error of about
+// e^3 < 2^-64, so the result is 1/x to within the FP64 rounding of its three
+// fused multiply-adds (about 1 ulp).  Three FP64 operations instead of the
+// ~8 pipe slots of an IEEE division.  (Inputs outside the positive normal
+// range, or so large that 1/x is subnormal -- a nonphysical state, which the
+// kernels report separately -- give a meaningless but finite value.)
 __device__ __forceinline__ double rcp_pos(double x) {
   const int hi = __double2hiint(x);
   const int ex = (hi >> 20) & 0x7FF;
-  const double m = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, __double2loint(x));
+  const float mf = __uint_as_float(
+      0x3F800000u | (__funnelshift_r((unsigned)__double2loint(x), (unsigned)hi, 29) & 0x7FFFFFu));
   float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__double2float_rn(m)));
-  double r = (double)rf;
-  r = __hiloint2double(__double2hiint(r) - ((ex - 1023) << 20), __double2loint(r));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+  const double r = f64_of_f32_pos(rf, 1023 - ex);
   const double e = fma(-x, r, 1.0);
   return fma(r, fma(e, e, e), r);
 }
@@ -151,13 +218,43 @@ __device__ __forceinline__ double rcp_pos(double x) {
 // least an ulp of them), so their weights keep dominating the others and
 // the flux moves by less than that 2^-80.
 //
-// mu is formed in FP32 from the FP64 differences: it enters only through
-// eps mu^2 with eps = 1e-40, which matters only for a substencil whose
-// indicator is below ~1e-30 mu^2, where a relative error of 1e-7 in mu moves
-// Gamma_k by the same relative amount and the weights by less than 1e-30.
-// Differences beyond FP32's range (a sum that overflows) take the same sum in
-// FP64; the rescale below relies on mu being right to within that 1e-7.
+// mu is formed in FP32 from the FP64 differences (truncated to FP32 after a
+// common power-of-two scaling, so no data magnitude overflows it), and
+// eps mu^2 from it to FP32 accuracy: it enters only through eps mu^2 with
+// eps = 1e-40, which matters only for a substencil whose indicator is below
+// ~1e-30 mu^2, where a relative error of ~1e-6 in eps mu^2 moves Gamma_k by
+// the same relative amount and the weights by less than 1e-30.  The rescale
+// below relies on eps mu^2 being right to within that 1e-6.
 // ---------------------------------------------------------------------------
+// The sensitivity term 4 eps mu^2 = (me dev + mo)^2 of eqs. (21)-(22) from
+// the FP32 deviation sum devf of a stencil scaled by 2^(1019 - es)
+// (dev = devf 2^(es - 1019)).  Flat stencil (devf = 0): mo^2.  Where
+// me dev >= 2^30 mo it is me^2 dev^2 to FP32 accuracy: with devf = mdf 2^edf,
+// the FP32 product y = mef mdf^2 in [1, 8) times 2^(eme + 2 edf +
+// 2 (es - 1019)), assembled on the integer pipe.  Otherwise (a variation below
+// ~1e-29 of the data, or exponents beyond FP64's range) dev64() -- the same
+// deviation sum in FP64 -- in a branch only the warps that need it run.
+template <class Dev64>
+__device__ __forceinline__ double sens_term(float devf, int es, const ReconParams &P,
+                                            Dev64 dev64) {
+  const unsigned db = __float_as_uint(devf);
+  const int edf = (int)(db >> 23) - 127;
+  const float mdf = __uint_as_float((db & 0x7FFFFFu) | 0x3F800000u);
+  const float y = P.mef * (mdf * mdf);
+  const int k = P.eme + 2 * (edf + es - 1019);
+  const int fexp = (int)(__float_as_uint(y) >> 23) + 896 + k;  // biased exponent of the result
+  const bool flat = (devf == 0.0f);
+  const bool fast = flat || (edf + es >= P.lthr && fexp > 0 && fexp < 2047);
+  double e = flat ? P.e0 : f64_of_f32_pos(y, fast ? k : 0);
+  if (__any_sync(__activemask(), !fast)) {
+    if (!fast) {
+      const double sm = fma(dev64(), P.me, P.mo);  // sqrt(4 eps) mu
+      e = sm * sm;
+    }
+  }
+  return e;
+}
+
 struct ZA6Part {
   double num, den;  // f = v2 + num / (6 den)
 };
@@ -173,22 +270,23 @@ __device__ __forceinline__ ZA6Part za6d(double d0, double d1, double d2, double 
   const double r5 = fma(3.0, s1 - s2, s3 - s0);
   double e;
   if (AI) {
-    // deviations from v2, then from their mean, in FP32
-    const float f0 = __double2float_rn(d0), f1 = __double2float_rn(d1),
-                f2 = __double2float_rn(d2), f3 = __double2float_rn(d3),
-                f4 = __double2float_rn(d4);
+    // deviations from v2, then from their mean, in FP32, on the differences
+    // scaled by 2^(1019 - es) with es the largest of their exponents (so no
+    // data range overflows FP32): dev = devf 2^(es - 1019)
+    const int es = max(max(max(__double2hiint(d0) & 0x7FFFFFFF, __double2hiint(d1) & 0x7FFFFFFF),
+                           max(__double2hiint(d2) & 0x7FFFFFFF, __double2hiint(d3) & 0x7FFFFFFF)),
+                       __double2hiint(d4) & 0x7FFFFFFF) >> 20;
+    const float f0 = f32_scaled(d0, es), f1 = f32_scaled(d1, es), f2 = f32_scaled(d2, es),
+                f3 = f32_scaled(d3, es), f4 = f32_scaled(d4, es);
     const float fa0 = -(f0 + f1), fa1 = -f1, fa3 = f2, fa4 = f2 + f3, fa5 = fa4 + f4;
     const float fm = ((fa0 + fa1) + (fa3 + fa4) + fa5) * (1.0f / 6.0f);
     const float devf = fabsf(fa0 - fm) + fabsf(fa1 - fm) + fabsf(fm) + fabsf(fa3 - fm) +
                        fabsf(fa4 - fm) + fabsf(fa5 - fm);
-    double dev = (double)devf;
-    if (!(devf <= 3.0e38f)) {  // differences beyond FP32's range: the same sum in FP64
+    e = sens_term(devf, es, P, [&]() {
       const double a0 = -(d0 + d1), a1 = -d1, a3 = d2, a4 = d2 + d3, a5 = a4 + d4;
       const double m = ((a0 + a1) + (a3 + a4) + a5) * (1.0 / 6.0);
-      dev = fabs(a0 - m) + fabs(a1 - m) + fabs(m) + fabs(a3 - m) + fabs(a4 - m) + fabs(a5 - m);
-    }
-    const double sm = fma(dev, P.me, P.mo);  // sqrt(4 eps) mu
-    e = sm * sm;
+      return fabs(a0 - m) + fabs(a1 - m) + fabs(m) + fabs(a3 - m) + fabs(a4 - m) + fabs(a5 - m);
+    });
   } else {
     e = P.efix;
   }
@@ -230,7 +328,20 @@ __device__ __forceinline__ ZA6Part za6d(double d0, double d1, double d2, double 
       b2 *= sc;
       b3 = bsum * (0.25 * sc);
     }
-    const double T = T0 * __longlong_as_double((2048LL - ex) << 52);  // 4 tau, scaled
+    // 4 tau, scaled by the same 2^(1023 - ex) (T0 times 2^(1025 - ex)): an add
+    // to the exponent field for a normal T0; 0 when the scaled value falls
+    // below the normal range (it is then under 2^-1022 of the largest b_k and
+    // moves no weight); a subnormal T0 takes the multiplication, in a branch
+    // only the warps that need it run.
+    const long long tb = __double_as_longlong(T0);
+    const int t0e = (int)(tb >> 52);
+    double T = (t0e > 0 && t0e + 1025 - ex > 0)
+                   ? __longlong_as_double(tb + ((long long)(1025 - ex) << 52))
+                   : 0.0;
+    const bool sub = (t0e == 0 && tb != 0);
+    if (__any_sync(__activemask(), sub)) {
+      if (sub) T = T0 * __longlong_as_double((2048LL - ex) << 52);
+    }
     const long long floor_bits = (1023LL - 166) << 52;  // 2^-166 (b_3 >= max / 4 needs none)
     b0 = __longlong_as_double(max(__double_as_longlong(b0), floor_bits));
     b1 = __longlong_as_double(max(__double_as_longlong(b1), floor_bits));
@@ -423,29 +534,31 @@ __device__ __forceinline__ RPart za_r(const double (&v)[2 * R], const ReconParam
 #pragma unroll
   for (int j = 0; j < N; ++j) w[j] = (j == R - 1) ? 0.0 : v[j] - vc;
   double e;
-  if (AI) {  // mu from FP32 deviations, as in za6 (FP64 beyond FP32's range)
+  if (AI) {  // mu from FP32 deviations, as in za6d (dev = 6/N of the sum over N points)
+    int es = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j != R - 1) es = max(es, __double2hiint(w[j]) & 0x7FFFFFFF);
+    es >>= 20;
     float wf[N], mf = 0.0f;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      wf[j] = (j == R - 1) ? 0.0f : __double2float_rn(w[j]);
+      wf[j] = (j == R - 1) ? 0.0f : f32_scaled(w[j], es);
       mf += wf[j];
     }
     mf *= 1.0f / N;
     float df = 0.0f;
 #pragma unroll
     for (int j = 0; j < N; ++j) df += fabsf(wf[j] - mf);
-    double dev = (double)df;
-    if (!(df <= 3.0e38f)) {
-      dev = 0.0;
-      double m = 0.0;
+    e = sens_term(df * (6.0f / N), es, P, [&]() {
+      double m = 0.0, dev = 0.0;
 #pragma unroll
       for (int j = 0; j < N; ++j) m += w[j];
       m *= 1.0 / N;
 #pragma unroll
       for (int j = 0; j < N; ++j) dev += fabs(w[j] - m);
-    }
-    const double sm = fma(dev, P.me * (6.0 / N), P.mo);  // sqrt(4 eps) mu
-    e = sm * sm;
+      return dev * (6.0 / N);
+    });
   } else {
     e = P.efix;
   }
@@ -639,21 +752,33 @@ __device__ __forceinline__ float za6_f32(float e0, float e1, float e2, float e3,
 template <bool P1>
 __device__ __forceinline__ double field_flux_f32(const double (&w)[6], const double (&g)[6],
                                                  double A, const Recon32 &P) {
-  const float Af = (float)A;
+  // The differences go to FP32 scaled by the common power of two 2^(1019 - es)
+  // (es: their largest exponent; the reconstruction is homogeneous of degree
+  // one in the data, so the correction comes back times 2^(es - 1019)), with
+  // the format changes on the integer pipe.
+  const float Af = f32_rn(A);
+  double dw[5], dg[5];
+  int es = 0;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    dw[j] = w[j + 1] - w[j];
+    dg[j] = g[j + 1] - g[j];
+    es = max(es, max(__double2hiint(dw[j]) & 0x7FFFFFFF, __double2hiint(dg[j]) & 0x7FFFFFFF));
+  }
+  es >>= 20;
   float dp[5], dm[5];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
-    const float dw = __double2float_rn(w[j + 1] - w[j]);
-    const float dg = __double2float_rn(g[j + 1] - g[j]);
-    dp[j] = fmaf(Af, dw, dg);
-    dm[j] = fmaf(-Af, dw, dg);
+    const float fw = f32_scaled_rn(dw[j], es), fg = f32_scaled_rn(dg[j], es);
+    dp[j] = fmaf(Af, fw, fg);
+    dm[j] = fmaf(-Af, fw, fg);
   }
   // f^+ on (i-2..i+3) around v2 = f^+_i; f^- mirrored (i+3..i-2) around f^-_{i+1},
   // whose differences are -dm[4], ..., -dm[0].
   const float cp = za6_f32<P1>(dp[0], dp[1], dp[2], dp[3], dp[4], P);
   const float cm = za6_f32<P1>(-dm[4], -dm[3], -dm[2], -dm[1], -dm[0], P);
   const double base = fma(A, w[2] - w[3], g[2] + g[3]);
-  return base + (double)(cp + cm);
+  return base + f64_of_f32(cp + cm, es - 1019);
 }
 
 // ---------------------------------------------------------------------------

@@ -143,6 +143,22 @@ __device__ __forceinline__ ReconParams make_rp(const StageArgs &a, double k) {
   const double se = sqrt(4.0 * a.eps);
   r.me = se * (1.0 / 6.0);
   r.mo = se * (k * a.mu0);
+  r.e0 = r.mo * r.mo;
+  // me^2 = eps / 9 as an FP32 mantissa and an exponent (eps / 9 is a normal
+  // double for every eps the boundary accepts with Ai)
+  const double me2 = a.eps * (1.0 / 9.0);
+  const int hi = __double2hiint(me2);
+  r.eme = ((hi >> 20) & 0x7FF) - 1023;
+  r.mef = __uint_as_float(0x3F800000u |
+                          (__funnelshift_r((unsigned)__double2loint(me2), (unsigned)hi, 29) & 0x7FFFFFu));
+  // dev >= 2^(lthr - 1019) implies dev / 6 >= 2^30 scale mu_0: with
+  // 6 scale mu_0 < 2^(E + 1), E its exponent, lthr = 1019 + E + 1 + 30
+  if (a.mu0 > 0.0) {
+    const double m6 = 6.0 * k * a.mu0;
+    r.lthr = 1019 + (((__double2hiint(m6) >> 20) & 0x7FF) - 1023) + 31;
+  } else {
+    r.lthr = -(1 << 20);
+  }
   return r;
 }
 
