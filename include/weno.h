@@ -223,10 +223,11 @@ weno_status weno_dd_stage(const weno_desc *d, int64_t nrows, int stage, double *
  * GPU that loads it until the process exits; the call allocates nothing.
  * Limits: nbatch <= 1020 (larger batches return WENO_ERR_ARG with a message;
  * use weno_rhs).  The first call on each device looks up the array's address
- * (make it before any stream capture).  All calls share the array and clear
- * what they need; calls that overlap on the GPU race and must be serialised by
- * the caller.  U, dUdt: DEVICE arrays as for weno_rhs.  Synchronises the
- * stream and returns WENO_ERR_NONPHYSICAL for a nonphysical input. */
+ * (make it before any stream capture on that device).  All calls share the
+ * array and clear what they need; calls that overlap on the GPU race and must
+ * be serialised by the caller.  U, dUdt: DEVICE arrays as for weno_rhs.  Every
+ * call ends by synchronising `stream` to read the shared status word back, and
+ * returns WENO_ERR_NONPHYSICAL for a nonphysical input. */
 weno_status weno_rhs_noalloc(const weno_desc *d, const double *U, double *dUdt, void *stream);
 
 /* ---------------------------------------------------------------------------

@@ -13,8 +13,10 @@
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress while that device is current, and caches it; make
-// that first call before any stream capture.  Host code never uses the
-// array's name as a pointer (on the host it is only a stand-in for the symbol).
+// that first call before any stream capture on that device.  Host code never
+// uses the array's name as a pointer (on the host it is only a stand-in for
+// the symbol).  Every call ends by synchronising its stream, to read the
+// shared status word back.
 //
 // Sharing: every call on a device uses the same array.  Each call clears the
 // parts that must start at zero; calls whose work overlaps on the GPU (on two
