@@ -177,6 +177,31 @@ __device__ __forceinline__ double rcp_pos(double x) {
   return fma(r, fma(e, e, e), r);
 }
 
+// 1/sqrt(x) for a positive normal x, by the same route as rcp_pos: with
+// x = m' 2^(2q), m' in [1, 4), the FP32 approximate reciprocal square root of
+// m' (rsqrt.approx.ftz.f32, within about 2^-22 after m' is truncated to FP32)
+// scaled by 2^-q on the integer pipe, then one step of the third-order
+// iteration r <- r (1 + e/2 + 3 e^2 / 8), e = 1 - x r^2 (the series of
+// (1 - e)^(-1/2)), which leaves a relative error of about 2.5 e^3 / 8 <
+// 2^-64: five FP64 operations.  (Outside the positive normal range -- a
+// nonphysical state, reported separately -- the value is meaningless.)
+__device__ __forceinline__ double rsqrt_pos(double x) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7FF;
+  const int odd = (ex & 1) ^ 1;  // the unbiased exponent ex - 1023 is odd
+  const float mf = __uint_as_float(((unsigned)(127 + odd) << 23) |
+                                   (__funnelshift_r((unsigned)__double2loint(x), (unsigned)hi, 29) &
+                                    0x7FFFFFu));
+  float rf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+  const double r = f64_of_f32_pos(rf, (1023 + odd - ex) / 2);  // times 2^-q, q = (ex - 1023 - odd) / 2
+  const double e = fma(-x, r * r, 1.0);
+  return fma(r * fma(0.375, e, 0.5), e, r);
+}
+
+// sqrt(x) = x / sqrt(x) for a positive normal x (six FP64 operations).
+__device__ __forceinline__ double sqrt_pos(double x) { return x * rsqrt_pos(x); }
+
 // ---------------------------------------------------------------------------
 // WENO-ZA6 numerical flux at x_{i+1/2} from v0..v5 = f_{i-2}..f_{i+3}
 // (positive flux; the negative flux is this routine on the mirrored stencil).
@@ -203,8 +228,10 @@ __device__ __forceinline__ double rcp_pos(double x) {
 // mu^2 and e = 4e-40 mu^2, so min b / max b > ~1e-44.)
 //
 // For p = 1 the four divisions tau/b_k are removed: a_k is proportional to
-// (b_k + 4 tau) prod_{j != k} b_j = P + 4 tau Q_k with P = prod b_j and
-// Q_k = prod_{j != k} b_j (one fused multiply-add each).  Before the
+// (b_k + 4 tau) prod_{j != k} b_j, formed pairwise: with p01 = b0 b1 and
+// p23 = b2 b3, a_0 = p23 (p01 + 4 tau b1), a_1 = p23 (p01 + 4 tau b0),
+// a_2 = p01 (p23 + 4 tau b3), a_3 = p01 (p23 + 4 tau b2), and the sums over
+// k = 0, 1 and k = 2, 3 are taken before their factors p23, p01.  Before the
 // products, the b_k and 4 tau are multiplied by the power of two that brings
 // their maximum into [1, 2) (built from the exponent bits), and the scaled
 // b_k are floored at 2^-166, so the products -- and the product of two
@@ -346,12 +373,17 @@ __device__ __forceinline__ ZA6Part za6d(double d0, double d1, double d2, double 
     b0 = __longlong_as_double(max(__double_as_longlong(b0), floor_bits));
     b1 = __longlong_as_double(max(__double_as_longlong(b1), floor_bits));
     b2 = __longlong_as_double(max(__double_as_longlong(b2), floor_bits));
+    // a_0 = p23 x0, a_1 = p23 x1, a_2 = p01 x2, a_3 = p01 x3 with p01 = b0 b1,
+    // p23 = b2 b3 and x0 = b1 (b0 + T) = p01 + T b1, x1 = p01 + T b0,
+    // x2 = p23 + T b3, x3 = p23 + T b2; the linear weights 1 : 9 : 9 : 1 go
+    // on x1, x2, and each half's sums are taken before its common factor
     const double p01 = b0 * b1, p23 = b2 * b3;
-    const double Pall = p01 * p23;
-    a0 = fma(T, b1 * p23, Pall);
-    a1 = fma(T, b0 * p23, Pall);
-    a2 = fma(T, b3 * p01, Pall);
-    a3 = fma(T, b2 * p01, Pall);
+    const double x0 = fma(T, b1, p01), y1 = 9.0 * fma(T, b0, p01);
+    const double y2 = 9.0 * fma(T, b3, p23), x3 = fma(T, b2, p23);
+    ZA6Part o;
+    o.num = fma(p23, fma(y1, r1, x0 * r0), p01 * fma(y2, r2, x3 * r3));
+    o.den = fma(p23, x0 + y1, p01 * (y2 + x3));
+    return o;
   } else {
     const double T = 4.0 * T0;
     const double b3 = 0.25 * bsum;
@@ -813,7 +845,7 @@ __device__ __forceinline__ bool roe_face(double sl, double unl, double utl, doub
   f.hq2 = 0.5 * q2;
   const double c2 = gm1 * (f.H - f.hq2);
   if (!pos_finite(c2)) return false;
-  f.ic = rsqrt(c2);
+  f.ic = rsqrt_pos(c2);
   f.c = c2 * f.ic;
   f.b1 = gm1 * (f.ic * f.ic);
   f.b2 = f.b1 * f.hq2;

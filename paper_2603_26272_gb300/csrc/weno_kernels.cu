@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_alpha(const AlphaArgs a) {
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < plane;
        k += (long long)gridDim.x * blockDim.x) {
     const double rho = Ub[k];
-    const double ir = 1.0 / rho;
+    const double ir = rcp_pos(rho);
     const double mx = Ub[plane + k];
     const double my = (a.nc == 4) ? Ub[2 * plane + k] : 0.0;
     const double E = Ub[(a.nc - 1) * plane + k];
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_alpha(const AlphaArgs a) {
     const double p = gm1 * (E - 0.5 * fma(mx, u, my * v));
     if (!(pos_finite(rho) && pos_finite(p)))
       record_status(a.status, 3, 0, b, k / a.nx, k % a.nx);
-    const double cs = sqrt(a.gamma * p * ir);
+    const double cs = sqrt_pos(a.gamma * p * ir);
     vm[0] = max(vm[0], abs_bits(u - cs));
     vm[1] = max(vm[1], abs_bits(u));
     vm[2] = max(vm[2], abs_bits(u + cs));

@@ -366,7 +366,7 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       }
     }
     const double rho = src[o], mx = src[pst + o], my = src[2 * pst + o], E = src[3 * pst + o];
-    const double rs = rsqrt(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
+    const double rs = rsqrt_pos(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
     const double ir = rs * rs;
     const double u = mx * ir, v = my * ir;
     const double p = gm1 * (E - 0.5 * fma(mx, u, my * v));
@@ -520,7 +520,7 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       const double u = uo[1] * ir, v = uo[2] * ir;
       const double p = gm1 * (uo[3] - 0.5 * fma(uo[1], u, uo[2] * v));
       if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
-      const double cs = sqrt(a.gamma * p * ir);
+      const double cs = sqrt_pos(a.gamma * p * ir);
       mx6[0] = max(mx6[0], abs_bits(u - cs));
       mx6[1] = max(mx6[1], abs_bits(u));
       mx6[2] = max(mx6[2], abs_bits(u + cs));
@@ -594,7 +594,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
       pl[1][k] = scalar_flux(a.system, a.adv_speed, u);
     } else {
       const double rho = Ub[gi], m = Ub[nx + gi], E = Ub[2 * nx + gi];
-      const double rs = rsqrt(rho);
+      const double rs = rsqrt_pos(rho);
       const double ir = rs * rs;
       const double u = m * ir;
       const double p = gm1 * (E - 0.5 * (m * u));
@@ -812,7 +812,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
       const double u = uo[1] * ir;
       const double p = gm1 * (uo[NC - 1] - 0.5 * (uo[1] * u));
       if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, 0, gi);
-      const double cs = sqrt(a.gamma * p * ir);
+      const double cs = sqrt_pos(a.gamma * p * ir);
       m3v[0] = abs_bits(u - cs);
       m3v[1] = abs_bits(u);
       m3v[2] = abs_bits(u + cs);
