@@ -109,13 +109,13 @@ weno_status weno_wavespeeds(const weno_desc *d, const double *U, double *alpha, 
                             void *ws, size_t ws_bytes, void *stream);
 
 /* Tile autotuning (2D, order 6).  weno_rhs, weno_step and weno_solve choose
- * among nine tile shapes of the 2D stage kernel (all give bitwise the same
+ * among eleven tile shapes of the 2D stage kernel (all give bitwise the same
  * result).  The first such call on a new problem shape (nx, ny, nbatch,
  * precision, ai, p == 1) in a process times them on the caller's data: two
  * launches of each shape on `stream`, writing only the workspace, with CUDA
  * events, and it synchronises the stream before it returns.  Later calls on
  * that shape are asynchronous as stated.  The environment variable
- * WENO_TILE2D = 0..8 forces one shape and skips the timing (use it when the
+ * WENO_TILE2D = 0..10 forces one shape and skips the timing (use it when the
  * first call must not synchronise, e.g. inside a stream capture). */
 
 /* Right-hand side of one Runge-Kutta stage, L(U) (eq. (5) dimension by

@@ -429,6 +429,25 @@ __device__ __forceinline__ double field_flux(const double (&w)[6], const double 
                    za6d<AI, P1>(dm[0], dm[1], dm[2], dm[3], dm[4], P));
 }
 
+// The same from the differences alone: dw[j] = w_{j+1} - w_j and
+// dg[j] = g_{j+1} - g_j over the six stencil cells.  Returns h less the
+// centre values g_i + g_{i+1}, i.e. the dissipation -A (w_{i+1} - w_i) plus
+// the two reconstructions' corrections; the caller adds the centre values
+// back (the 2D kernel in physical form after the back-projection, where
+// R (g_i + g_{i+1}) is the physical F_i + F_{i+1}).
+template <bool AI, bool P1>
+__device__ __forceinline__ double field_flux_d(const double (&dw)[5], const double (&dg)[5],
+                                               double A, const ReconParams &P) {
+  double dp[5], dm[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    dp[j] = fma(A, dw[j], dg[j]);
+    dm[4 - j] = fma(A, dw[j], -dg[j]);
+  }
+  return pair_flux(-A * dw[2], za6d<AI, P1>(dp[0], dp[1], dp[2], dp[3], dp[4], P),
+                   za6d<AI, P1>(dm[0], dm[1], dm[2], dm[3], dm[4], P));
+}
+
 // ---------------------------------------------------------------------------
 // Central-upwind WENO of order 2R for R = 2, 4, 5 (the Appendix schemes; R = 3
 // uses za6 above).  Tables as printed in the Appendix, divided out; rows the
@@ -777,26 +796,20 @@ __device__ __forceinline__ float za6_f32(float e0, float e1, float e2, float e3,
   return (c * (1.0f / 6.0f)) * mu;
 }
 
-// One characteristic field in FP32-reconstruction mode: w[j], g[j] are the
-// FP64 projections of the six stencil states and fluxes, A the field's GLF
-// speed.  Returns h = f_hat^+ + f_hat^- (kernel scaling: split without 1/2).
-// FP64 work: the ten differences, the base f+_i + f-_{i+1} and one add.
+// The FP32 part from the FP64 differences dw[j] = w_{j+1} - w_j, dg[j]:
+// the corrections of both reconstructions, c+ + c-, as an FP64 number.  The
+// differences go to FP32 scaled by the common power of two 2^(1019 - es)
+// (es: their largest exponent; the reconstruction is homogeneous of degree
+// one in the data, so the correction comes back times 2^(es - 1019)), with
+// the format changes on the integer pipe.
 template <bool P1>
-__device__ __forceinline__ double field_flux_f32(const double (&w)[6], const double (&g)[6],
+__device__ __forceinline__ double recon_pair_f32(const double (&dw)[5], const double (&dg)[5],
                                                  double A, const Recon32 &P) {
-  // The differences go to FP32 scaled by the common power of two 2^(1019 - es)
-  // (es: their largest exponent; the reconstruction is homogeneous of degree
-  // one in the data, so the correction comes back times 2^(es - 1019)), with
-  // the format changes on the integer pipe.
   const float Af = f32_rn(A);
-  double dw[5], dg[5];
   int es = 0;
 #pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    dw[j] = w[j + 1] - w[j];
-    dg[j] = g[j + 1] - g[j];
+  for (int j = 0; j < 5; ++j)
     es = max(es, max(__double2hiint(dw[j]) & 0x7FFFFFFF, __double2hiint(dg[j]) & 0x7FFFFFFF));
-  }
   es >>= 20;
   float dp[5], dm[5];
 #pragma unroll
@@ -809,8 +822,32 @@ __device__ __forceinline__ double field_flux_f32(const double (&w)[6], const dou
   // whose differences are -dm[4], ..., -dm[0].
   const float cp = za6_f32<P1>(dp[0], dp[1], dp[2], dp[3], dp[4], P);
   const float cm = za6_f32<P1>(-dm[4], -dm[3], -dm[2], -dm[1], -dm[0], P);
+  return f64_of_f32(cp + cm, es - 1019);
+}
+
+// One characteristic field in FP32-reconstruction mode: w[j], g[j] are the
+// FP64 projections of the six stencil states and fluxes, A the field's GLF
+// speed.  Returns h = f_hat^+ + f_hat^- (kernel scaling: split without 1/2).
+// FP64 work: the ten differences, the base f+_i + f-_{i+1} and one add.
+template <bool P1>
+__device__ __forceinline__ double field_flux_f32(const double (&w)[6], const double (&g)[6],
+                                                 double A, const Recon32 &P) {
+  double dw[5], dg[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    dw[j] = w[j + 1] - w[j];
+    dg[j] = g[j + 1] - g[j];
+  }
   const double base = fma(A, w[2] - w[3], g[2] + g[3]);
-  return base + f64_of_f32(cp + cm, es - 1019);
+  return base + recon_pair_f32<P1>(dw, dg, A, P);
+}
+
+// field_flux_f32 from the differences alone, less the centre values
+// g_i + g_{i+1} (as field_flux_d).
+template <bool P1>
+__device__ __forceinline__ double field_flux_f32d(const double (&dw)[5], const double (&dg)[5],
+                                                  double A, const Recon32 &P) {
+  return fma(-A, dw[2], recon_pair_f32<P1>(dw, dg, A, P));
 }
 
 // ---------------------------------------------------------------------------

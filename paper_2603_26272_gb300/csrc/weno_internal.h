@@ -15,7 +15,7 @@ struct DevStatus {
 };
 
 // 2D tile variants of the single-problem stage kernel (see launch_stage_t).
-constexpr int kTileVariants = 9;
+constexpr int kTileVariants = 11;
 
 // Everything one stage launch needs (passed by value).
 struct StageArgs {

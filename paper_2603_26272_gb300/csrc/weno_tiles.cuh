@@ -245,36 +245,188 @@ __device__ __forceinline__ void tma_issue_box(const CUtensorMap *tm, unsigned ba
 // 2 GHz; the copy of one box takes microseconds).
 constexpr long long kTmaWaitCycles = 2000000;
 
+// The TMA copy of tile (i0, j0)'s box of problem b into `box` (every thread
+// of the block calls this).  Returns false -- after recording
+// WENO_ERR_TIMEOUT and a second bounded wait for the copy in flight, which
+// writes into this block's shared memory -- when the copy did not complete
+// in time; the tile is then left undone.
+template <int TX, int TY, int R>
+__device__ bool tma_stage_box(const StageArgs &a, const CUtensorMap *tm, double *box, long long b,
+                              long long i0, long long j0) {
+  __shared__ __align__(8) unsigned long long s_bar;
+  const unsigned bar = smem_u32(&s_bar);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (a.tma_no_copy)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                   "r"((unsigned)tma_box_bytes<TX, TY, R>())
+                   : "memory");
+    else
+      tma_issue_box(tm, bar, box, (int)(i0 - TmaBox<R>::XO), (int)(j0 - R), (int)(b * 4),
+                    (unsigned)tma_box_bytes<TX, TY, R>());
+  }
+  long long t_start = clock64();
+  bool done = false;
+  while (!(done = mbar_try_wait(bar, 0)) && clock64() - t_start < kTmaWaitCycles) {
+  }
+  if (!__syncthreads_and(done)) {
+    if (tid == 0) record_status(a.status, 5, a.stage, b, j0, i0);
+    t_start = clock64();
+    while (!mbar_try_wait(bar, 0) && clock64() - t_start < kTmaWaitCycles) {
+    }
+    return false;
+  }
+  return true;
+}
+
+// Where staged cell (r, c) of tile (i0, j0) -- r in [0, TY + 2R), c in
+// [0, TX + 2R), the tile's cells at [R, R + TY) x [R, R + TX) -- is read from
+// without TMA: the array src with plane stride pst and offset o (the stage
+// input, or a neighbour's halo rows of a domain split), after the ghost rule
+// of each boundary; (gj, gi) is the cell reported on error.
+__device__ __forceinline__ void cell_source(const StageArgs &a, const double *Ub, long long b,
+                                            long long i0, long long j0, int R, int r, int c,
+                                            const double *&src, long long &o, long long &pst,
+                                            long long &gj, long long &gi) {
+  gi = ghost(i0 - R + c, a.nx, a.bc_x);
+  const long long jj = j0 - R + r;
+  src = Ub;
+  pst = a.nx * a.ny;
+  gj = jj;
+  if (jj < 0 && a.halo_lo) {  // a neighbour's rows below this strip
+    src = a.halo_lo + b * 4 * (R * a.nx);
+    o = (jj + R) * a.nx + gi;
+    pst = R * a.nx;
+  } else if (jj >= a.ny && a.halo_hi) {  // above it (rows beyond ny+R-1 only
+    src = a.halo_hi + b * 4 * (R * a.nx);  // fill a partial tile: any halo row)
+    o = min(jj - a.ny, (long long)(R - 1)) * a.nx + gi;
+    pst = R * a.nx;
+  } else {
+    gj = ghost(jj, a.ny, a.bc_y);
+    o = gj * a.nx + gi;
+  }
+}
+
+// Phase 3 of a 2D tile: per cell the conservative difference of eq. (5)
+// from the faces' 4 F (backproject4, so idx = 0.25 / dx, idy = 0.25 / dy), the
+// Runge-Kutta combination with the staged input u_at(r, c, q) of tile cell
+// (r, c), the strips' send rows, and the next stage's speed maxima.
+template <int TX, int TY, int R, class UAt>
+__device__ __forceinline__ void tile2d_update(const StageArgs &a, long long b, long long i0,
+                                              long long j0, double dt, const double *fx,
+                                              const double *fy, double idx, double idy,
+                                              UAt u_at) {
+  const long long plane = a.nx * a.ny;
+  const double gm1 = a.gamma - 1.0;
+  const int tid = threadIdx.x;
+  unsigned long long mx6[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+  const bool want_alpha = (a.mode == 0) && (a.alpha_out != nullptr);
+  for (int k = tid; k < TX * TY; k += blockDim.x) {
+    const int r = k / TX, c = k - r * TX;
+    const long long gi = i0 + c, gj = j0 + r;
+    if (gi >= a.nx || gj >= a.ny) continue;
+    const double *Fl = &fx[(r * (TX + 1) + c) * 4];
+    const double *Fr = Fl + 4;
+    const double *Gb = &fy[(r * TX + c) * 4];
+    const double *Gt = &fy[((r + 1) * TX + c) * 4];
+    const long long o = b * 4 * plane + gj * a.nx + gi;
+    double uo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double L = -(Fr[q] - Fl[q]) * idx - (Gt[q] - Gb[q]) * idy;
+      if (a.mode == 1) {
+        uo[q] = L;
+      } else {
+        const double base_s = fma(dt, L, u_at(r, c, q));
+        uo[q] = (a.a_n != 0.0) ? fma(a.a_n, a.Un[o + q * plane], a.a_s * base_s) : a.a_s * base_s;
+      }
+      a.Uout[o + q * plane] = uo[q];
+    }
+    if (a.send_lo && gj < R)  // edge rows of the output for the strips below / above
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a.send_lo[((b * 4 + q) * R + gj) * a.nx + gi] = uo[q];
+    if (a.send_hi && gj >= a.ny - R)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a.send_hi[((b * 4 + q) * R + (gj - (a.ny - R))) * a.nx + gi] = uo[q];
+    if (want_alpha) {
+      const double ir = rcp_pos(uo[0]);
+      const double u = uo[1] * ir, v = uo[2] * ir;
+      const double p = gm1 * (uo[3] - 0.5 * fma(uo[1], u, uo[2] * v));
+      if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
+      const double cs = sqrt_pos(a.gamma * p * ir);
+      mx6[0] = max(mx6[0], abs_bits(u - cs));
+      mx6[1] = max(mx6[1], abs_bits(u));
+      mx6[2] = max(mx6[2], abs_bits(u + cs));
+      mx6[3] = max(mx6[3], abs_bits(v - cs));
+      mx6[4] = max(mx6[4], abs_bits(v));
+      mx6[5] = max(mx6[5], abs_bits(v + cs));
+    }
+  }
+  if (want_alpha) {
+    const int slot[6] = {0, 1, 3, 4, 5, 7};
+    const int dup[6] = {-1, 2, -1, -1, 6, -1};
+    block_max_atomic<6>(mx6, a.alpha_out + b * 8, slot, dup);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// 2D Euler stage kernel.
+// 2D Euler stage kernel of the orders 4, 8, 10 (R = 2, 4, 5).
 // Shared planes per staged cell: 0 rho, 1 rho u, 2 rho v, 3 E, 4 u, 5 v, 6 H,
 // 7 sqrt(rho), 8 p (the fluxes are projected from u, v, p: project_flux4).
 // ---------------------------------------------------------------------------
-// One tile (tile index `tile` of problem b) of a 2D stage, run by one block.
-// R: half-width of the stencil (scheme of order 2R, halo of R cells).
-// sm: dynamic shared memory of smem_euler2d<TX, TY, R>() bytes.
 constexpr int kPlanes2D = 9;
 
-template <int TX, int TY, int R = 3>
-__host__ __device__ constexpr size_t smem_euler2d() {
+template <int TX, int TY, int R>
+__host__ __device__ constexpr size_t smem_euler2d_gen() {
   return sizeof(double) *
          (kPlanes2D * (TX + 2 * R) * (TY + 2 * R) + 4 * ((TX + 1) * TY + TX * (TY + 1)));
 }
 
-// Dynamic shared memory of a tile that may stage by TMA: the planes and
-// faces, then the box, 128-byte aligned.
+// Layout of the sixth-order tile (euler2d_tile6), in doubles, after the
+// 128-byte aligned start: box, Roe planes, cell-pair differences, faces.
+template <int TX, int TY> struct Tile6 {
+  static constexpr int R = 3, XO = TmaBox<3>::XO;
+  static constexpr int W = TX + 2 * R, HH = TY + 2 * R, BW = TX + 2 * XO, REG = W * HH;
+  static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+  static constexpr int NPX = TY * (W - 1), NPY = TX * (HH - 1);  // cell pairs of each sweep
+  static constexpr int ND = NPX > NPY ? NPX : NPY;
+  static constexpr int PB = HH * BW;  // plane stride of the box
+  static constexpr int kBox = 0, kPl = kBox + 4 * PB, kDd = kPl + 4 * REG, kFx = kDd + 7 * ND,
+                       kFy = kFx + 4 * NFX, kEnd = kFy + 4 * NFY;
+  static constexpr size_t kBytes = sizeof(double) * kEnd + 128;
+};
+
+// Dynamic shared memory of one 2D tile.
 template <int TX, int TY, int R = 3>
-__host__ __device__ constexpr size_t smem_euler2d_tma() {
-  return ((smem_euler2d<TX, TY, R>() + 127) & ~size_t(127)) + tma_box_bytes<TX, TY, R>() + 128;
+__host__ __device__ constexpr size_t smem_euler2d() {
+  return R == 3 ? Tile6<TX, TY>::kBytes : smem_euler2d_gen<TX, TY, R>();
 }
 
+// The same for a tile that may stage by TMA (orders 4, 8, 10: the planes and
+// faces, then the box, 128-byte aligned; the sixth-order layout always
+// holds the box).
+template <int TX, int TY, int R = 3>
+__host__ __device__ constexpr size_t smem_euler2d_tma() {
+  return R == 3 ? Tile6<TX, TY>::kBytes
+                : ((smem_euler2d_gen<TX, TY, R>() + 127) & ~size_t(127)) +
+                      tma_box_bytes<TX, TY, R>() + 128;
+}
+
+// One tile (tile index `tile` of problem b) of a 2D stage, run by one block.
+// R: half-width of the stencil (scheme of order 2R, halo of R cells).
+// sm: dynamic shared memory of smem_euler2d_tma<TX, TY, R>() bytes.
 // tm: tensor map of the stage input as [nbatch * 4][ny][nx] doubles, or NULL
 // (plain loads only; the serving engine and tiles of launches without one).
-template <int TX, int TY, bool AI, bool P1, int PREC, int R = 3>
-__device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, long long tile,
-                                             bool zeroing_block, double *sm,
-                                             const CUtensorMap *tm = nullptr) {
-  static_assert(R == 3 || PREC == 0, "FP32 reconstruction is sixth order only");
+template <int TX, int TY, bool AI, bool P1, int PREC, int R>
+__device__ __forceinline__ void euler2d_tile_gen(const StageArgs &a, long long b, long long tile,
+                                                 bool zeroing_block, double *sm,
+                                                 const CUtensorMap *tm) {
+  static_assert(R != 3 && PREC == 0, "orders 4, 8, 10 in FP64");
   constexpr int W = TX + 2 * R, HH = TY + 2 * R, REG = W * HH;
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
   constexpr int XO = TmaBox<R>::XO, BW = TX + 2 * XO;
@@ -296,41 +448,11 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
   // TMA staging of an interior tile: the box of the four conserved planes
   const bool use_tma = tm != nullptr && i0 - XO >= 0 && i0 - XO + BW <= a.nx && j0 - R >= 0 &&
                        j0 + TY + R <= a.ny;
-  const double *box = reinterpret_cast<const double *>(
-      (reinterpret_cast<uintptr_t>(sm) + ((smem_euler2d<TX, TY, R>() + 127) & ~size_t(127)) + 127) &
+  double *const box = reinterpret_cast<double *>(
+      (reinterpret_cast<uintptr_t>(sm) + ((smem_euler2d_gen<TX, TY, R>() + 127) & ~size_t(127)) +
+       127) &
       ~uintptr_t(127));
-  if (use_tma) {
-    __shared__ __align__(8) unsigned long long s_bar;
-    const unsigned bar = smem_u32(&s_bar);
-    if (tid == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-      if (a.tma_no_copy)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((unsigned)tma_box_bytes<TX, TY, R>())
-                     : "memory");
-      else
-        tma_issue_box(tm, bar, const_cast<double *>(box), (int)(i0 - XO), (int)(j0 - R),
-                      (int)(b * 4), (unsigned)tma_box_bytes<TX, TY, R>());
-    }
-    long long t_start = clock64();
-    bool done = false;
-    while (!(done = mbar_try_wait(bar, 0)) && clock64() - t_start < kTmaWaitCycles) {
-    }
-    if (!__syncthreads_and(done)) {
-      // The copy did not complete in time: report it (WENO_ERR_TIMEOUT),
-      // give the copy in flight one more bounded wait (it writes into this
-      // block's shared memory), and leave the tile undone.
-      if (tid == 0) record_status(a.status, 5, a.stage, b, j0, i0);
-      t_start = clock64();
-      while (!mbar_try_wait(bar, 0) && clock64() - t_start < kTmaWaitCycles) {
-      }
-      return;
-    }
-  }
+  if (use_tma && !tma_stage_box<TX, TY, R>(a, tm, box, b, i0, j0)) return;
 
   // Phase 1: stage the cross-shaped region (tile rows with x halo, tile
   // columns with y halo) and per-cell primitives / fluxes.
@@ -347,23 +469,7 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       gi = i0 - R + c;
       gj = j0 - R + r;
     } else {
-      gi = ghost(i0 - R + c, a.nx, a.bc_x);
-      const long long jj = j0 - R + r;
-      src = Ub;
-      pst = plane;
-      gj = jj;
-      if (jj < 0 && a.halo_lo) {  // a neighbour's rows below this strip
-        src = a.halo_lo + b * 4 * (R * a.nx);
-        o = (jj + R) * a.nx + gi;
-        pst = R * a.nx;
-      } else if (jj >= a.ny && a.halo_hi) {  // above it (rows beyond ny+R-1 only
-        src = a.halo_hi + b * 4 * (R * a.nx);  // fill a partial tile: any halo row)
-        o = min(jj - a.ny, (long long)(R - 1)) * a.nx + gi;
-        pst = R * a.nx;
-      } else {
-        gj = ghost(jj, a.ny, a.bc_y);
-        o = gj * a.nx + gi;
-      }
+      cell_source(a, Ub, b, i0, j0, R, r, c, src, o, pst, gj, gi);
     }
     const double rho = src[o], mx = src[pst + o], my = src[2 * pst + o], E = src[3 * pst + o];
     const double rs = rsqrt_pos(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
@@ -417,38 +523,7 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
       A1 = A2 = A3 = A4 = m;
     }
     double h1, h2, h3, h4;
-    if constexpr (PREC == 1) {
-      // FP32 reconstruction: FP64 projections, FP32 split and WENO-ZA6.
-      double W[4][6], G[4][6];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int k = base + j * stride;
-        project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], W[0][j],
-                 W[1][j], W[2][j], W[3][j]);
-        project_flux4(fs, pl[pun * REG + k], pl[8 * REG + k], W[0][j], W[1][j], W[2][j],
-                      W[3][j], G[0][j], G[1][j], G[2][j], G[3][j]);
-      }
-      const Recon32 r32 = make_r32(a);
-      h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
-      h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
-      h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
-      h4 = field_flux_f32<P1>(W[3], G[3], A4, r32);
-    } else if constexpr (R == 3) {
-      // WENO-ZA6: the projections, then per field the split differences
-      double W[4][6], G[4][6];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int k = base + j * stride;
-        project4(fs, pl[k], pl[pmn * REG + k], pl[pmt * REG + k], pl[3 * REG + k], W[0][j],
-                 W[1][j], W[2][j], W[3][j]);
-        project_flux4(fs, pl[pun * REG + k], pl[8 * REG + k], W[0][j], W[1][j], W[2][j],
-                      W[3][j], G[0][j], G[1][j], G[2][j], G[3][j]);
-      }
-      h1 = field_flux<AI, P1>(W[0], G[0], A1, rp4);
-      h2 = field_flux<AI, P1>(W[1], G[1], A2, rp2);
-      h3 = field_flux<AI, P1>(W[2], G[2], A3, rp2);
-      h4 = field_flux<AI, P1>(W[3], G[3], A4, rp4);
-    } else {
+    {
       // f^+ in stencil order, f^- mirrored (its upwind side is on the right).
       constexpr int N = 2 * R;
       double p1[N], p2[N], p3[N], p4[N], m1[N], m2[N], m3[N], m4[N];
@@ -482,58 +557,270 @@ __device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, lo
   }
   __syncthreads();
 
-  // Phase 3: conservative difference, RK combination, next-stage speeds.
-  // The faces hold 4 F (backproject4), so 1/4 goes with 1/dx, 1/dy.
-  const double idx = 0.25 / a.dx, idy = 0.25 / a.dy;
-  unsigned long long mx6[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-  const bool want_alpha = (a.mode == 0) && (a.alpha_out != nullptr);
-  for (int k = tid; k < TX * TY; k += blockDim.x) {
-    const int r = k / TX, c = k - r * TX;
-    const long long gi = i0 + c, gj = j0 + r;
-    if (gi >= a.nx || gj >= a.ny) continue;
-    const double *Fl = &fx[(r * (TX + 1) + c) * 4];
-    const double *Fr = Fl + 4;
-    const double *Gb = &fy[(r * TX + c) * 4];
-    const double *Gt = &fy[((r + 1) * TX + c) * 4];
-    const int kc = (R + r) * W + R + c;
-    const long long o = b * 4 * plane + gj * a.nx + gi;
-    double uo[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double L = -(Fr[q] - Fl[q]) * idx - (Gt[q] - Gb[q]) * idy;
-      if (a.mode == 1) {
-        uo[q] = L;
-      } else {
-        const double base_s = fma(dt, L, pl[q * REG + kc]);
-        uo[q] = (a.a_n != 0.0) ? fma(a.a_n, a.Un[o + q * plane], a.a_s * base_s) : a.a_s * base_s;
-      }
-      a.Uout[o + q * plane] = uo[q];
+  tile2d_update<TX, TY, R>(a, b, i0, j0, dt, fx, fy, 0.25 / a.dx, 0.25 / a.dy,
+                           [&](int r, int c, int q) { return pl[q * REG + (R + r) * W + R + c]; });
+}
+
+// ---------------------------------------------------------------------------
+// 2D Euler stage kernel of the sixth-order scheme (R = 3).
+//
+// The reconstruction of a face needs, per characteristic field, only the
+// differences of the split fluxes f+- = g +- alpha w over its six stencil
+// cells (field_flux_d), and those are L (F_{j+1} - F_j) +- alpha L (U_{j+1}
+// - U_j): the face's left eigenvectors applied to differences of the state
+// and of the physical flux between adjacent cells.  Those differences are
+// formed once per cell pair and direction and shared by the five faces whose
+// stencils hold the pair, so a face projects 10 difference vectors instead
+// of 6 states and 6 fluxes and subtracts nothing per field.  The centre
+// values g_i + g_{i+1} the reconstruction adds to its differences come back
+// through R as the physical 2 (F_i + F_{i+1}) = 2 (2 F_i + dF) (R L = I),
+// added after the back-projection.
+//
+// Phases: 1 stage the conserved variables (TMA or indexed loads) and the Roe
+// inputs; then per direction (x, then y) 1d the cell-pair differences and
+// 2d the faces; 3 the update (tile2d_update).  Shared memory: Tile6.
+// ---------------------------------------------------------------------------
+
+// Components 1..3 of the normal-frame physical flux of a cell (eq. (25)) from
+// its state and the staged u_n, H: with p = rho H - E, F1 = m_n u_n + p,
+// F2 = m_t u_n, F3 = H m_n (F0 = m_n).
+__device__ __forceinline__ void normal_flux(double rho, double mn, double mt, double E, double un,
+                                            double H, double &F1, double &F2, double &F3) {
+  const double p = fma(rho, H, -E);
+  F1 = fma(mn, un, p);
+  F2 = mt * un;
+  F3 = H * mn;
+}
+
+template <int TX, int TY, bool AI, bool P1, int PREC, int DIR>
+__device__ __forceinline__ void tile6_sweep(const StageArgs &a, long long b, long long i0,
+                                            long long j0, double gm1, double *sm,
+                                            const ReconParams &rp2, const ReconParams &rp4) {
+  using L = Tile6<TX, TY>;
+  constexpr int R = 3, W = L::W, BW = L::BW, XO = L::XO, PB = L::PB, REG = L::REG, ND = L::ND;
+  const double *const box = sm + L::kBox;
+  const double *const pl = sm + L::kPl;
+  double *const dd = sm + L::kDd;
+  double *const fo = sm + (DIR ? L::kFy : L::kFx);
+  const int tid = threadIdx.x;
+  // box offset of staged cell (r, c)
+  auto bo = [](int r, int c) { return r * BW + c + XO - R; };
+
+  // 1d: differences of each cell pair along DIR (normal frame: m_n = rho u
+  // for x, rho v for y), in dd[q * ND + pair]:
+  //   x: pair (rr, pc), rr in [0, TY), pc in [0, W - 1): cells (R + rr, pc), (R + rr, pc + 1)
+  //   y: pair (pr, cc), pr in [0, HH - 1), cc in [0, TX): cells (pr, R + cc), (pr + 1, R + cc)
+  constexpr int NP = DIR ? L::NPY : L::NPX;
+  for (int k = tid; k < NP; k += blockDim.x) {
+    int rA, cA, rB, cB;
+    if (DIR == 0) {
+      rA = R + k / (W - 1);
+      cA = k - (rA - R) * (W - 1);
+      rB = rA;
+      cB = cA + 1;
+    } else {
+      rA = k / TX;
+      cA = R + (k - rA * TX);
+      rB = rA + 1;
+      cB = cA;
     }
-    if (a.send_lo && gj < R)  // edge rows of the output for the strips below / above
-#pragma unroll
-      for (int q = 0; q < 4; ++q) a.send_lo[((b * 4 + q) * R + gj) * a.nx + gi] = uo[q];
-    if (a.send_hi && gj >= a.ny - R)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) a.send_hi[((b * 4 + q) * R + (gj - (a.ny - R))) * a.nx + gi] = uo[q];
-    if (want_alpha) {
-      const double ir = rcp_pos(uo[0]);
-      const double u = uo[1] * ir, v = uo[2] * ir;
-      const double p = gm1 * (uo[3] - 0.5 * fma(uo[1], u, uo[2] * v));
-      if (!(pos_finite(uo[0]) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
-      const double cs = sqrt_pos(a.gamma * p * ir);
-      mx6[0] = max(mx6[0], abs_bits(u - cs));
-      mx6[1] = max(mx6[1], abs_bits(u));
-      mx6[2] = max(mx6[2], abs_bits(u + cs));
-      mx6[3] = max(mx6[3], abs_bits(v - cs));
-      mx6[4] = max(mx6[4], abs_bits(v));
-      mx6[5] = max(mx6[5], abs_bits(v + cs));
+    const int oA = bo(rA, cA), oB = bo(rB, cB), kA = rA * W + cA, kB = rB * W + cB;
+    const double rhoA = box[oA], mnA = box[(1 + DIR) * PB + oA], mtA = box[(2 - DIR) * PB + oA],
+                 EA = box[3 * PB + oA];
+    const double rhoB = box[oB], mnB = box[(1 + DIR) * PB + oB], mtB = box[(2 - DIR) * PB + oB],
+                 EB = box[3 * PB + oB];
+    double F1A, F2A, F3A, F1B, F2B, F3B;
+    normal_flux(rhoA, mnA, mtA, EA, pl[(1 + DIR) * REG + kA], pl[3 * REG + kA], F1A, F2A, F3A);
+    normal_flux(rhoB, mnB, mtB, EB, pl[(1 + DIR) * REG + kB], pl[3 * REG + kB], F1B, F2B, F3B);
+    dd[0 * ND + k] = rhoB - rhoA;
+    dd[1 * ND + k] = mnB - mnA;  // also dF0
+    dd[2 * ND + k] = mtB - mtA;
+    dd[3 * ND + k] = EB - EA;
+    dd[4 * ND + k] = F1B - F1A;
+    dd[5 * ND + k] = F2B - F2A;
+    dd[6 * ND + k] = F3B - F3A;
+  }
+  __syncthreads();
+
+  // 2d: the faces along DIR.  x-face (fr, fc): between cells (R + fr, R - 1 + fc)
+  // and (R + fr, R + fc), stencil pairs fr (W - 1) + fc + j; y-face (fr, fc):
+  // between (R - 1 + fr, R + fc) and (R + fr, R + fc), pairs (fr + j) TX + fc.
+  constexpr int NF = DIR ? L::NFY : L::NFX;
+  const unsigned long long *al = a.alpha_in + b * 8 + 4 * DIR;
+  double A1 = bits2d(al[0]), A2 = bits2d(al[1]), A3 = bits2d(al[2]), A4 = bits2d(al[3]);
+  if (a.alpha_single) {
+    const double m = fmax(fmax(A1, A2), fmax(A3, A4));
+    A1 = A2 = A3 = A4 = m;
+  }
+  const Recon32 r32 = make_r32(a);
+  for (int f = tid; f < NF; f += blockDim.x) {
+    int fr, fc, p0, rL, cL, rR, cR;
+    constexpr int PS = DIR ? TX : 1;  // pair stride along the stencil
+    if (DIR == 0) {
+      fr = f / (TX + 1);
+      fc = f - fr * (TX + 1);
+      p0 = fr * (W - 1) + fc;
+      rL = R + fr;
+      cL = R - 1 + fc;
+      rR = rL;
+      cR = cL + 1;
+    } else {
+      fr = f / TX;
+      fc = f - fr * TX;
+      p0 = fr * TX + fc;
+      rL = R - 1 + fr;
+      cL = R + fc;
+      rR = rL + 1;
+      cR = cL;
     }
+    const int kL = rL * W + cL, kR = rR * W + cR;
+    FaceState fs;
+    if (!roe_face(pl[kL], pl[(1 + DIR) * REG + kL], pl[(2 - DIR) * REG + kL], pl[3 * REG + kL],
+                  pl[kR], pl[(1 + DIR) * REG + kR], pl[(2 - DIR) * REG + kR], pl[3 * REG + kR],
+                  gm1, fs))
+      record_status(a.status, 3, a.stage, b, j0 + fr, i0 + fc);
+    double dw[4][5], dg[4][5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int pj = p0 + j * PS;
+      const double dmn = dd[ND + pj];
+      project4(fs, dd[pj], dmn, dd[2 * ND + pj], dd[3 * ND + pj], dw[0][j], dw[1][j], dw[2][j],
+               dw[3][j]);
+      project4(fs, dmn, dd[4 * ND + pj], dd[5 * ND + pj], dd[6 * ND + pj], dg[0][j], dg[1][j],
+               dg[2][j], dg[3][j]);
+    }
+    double h1, h2, h3, h4;
+    if constexpr (PREC == 1) {
+      h1 = field_flux_f32d<P1>(dw[0], dg[0], A1, r32);
+      h2 = field_flux_f32d<P1>(dw[1], dg[1], A2, r32);
+      h3 = field_flux_f32d<P1>(dw[2], dg[2], A3, r32);
+      h4 = field_flux_f32d<P1>(dw[3], dg[3], A4, r32);
+    } else {
+      h1 = field_flux_d<AI, P1>(dw[0], dg[0], A1, rp4);
+      h2 = field_flux_d<AI, P1>(dw[1], dg[1], A2, rp2);
+      h3 = field_flux_d<AI, P1>(dw[2], dg[2], A3, rp2);
+      h4 = field_flux_d<AI, P1>(dw[3], dg[3], A4, rp4);
+    }
+    double F0, F1, F2, F3;
+    backproject4(fs, h1, h2, h3, h4, F0, F1, F2, F3);
+    // the centre values: 4 F_hat += 2 (F_L + F_R) = 4 F_L + 2 dF of the centre pair
+    {
+      const int oL = bo(rL, cL), pc = p0 + 2 * PS;
+      const double mnL = box[(1 + DIR) * PB + oL];
+      double FL1, FL2, FL3;
+      normal_flux(box[oL], mnL, box[(2 - DIR) * PB + oL], box[3 * PB + oL],
+                  pl[(1 + DIR) * REG + kL], pl[3 * REG + kL], FL1, FL2, FL3);
+      F0 = fma(4.0, mnL, fma(2.0, dd[ND + pc], F0));
+      F1 = fma(4.0, FL1, fma(2.0, dd[4 * ND + pc], F1));
+      F2 = fma(4.0, FL2, fma(2.0, dd[5 * ND + pc], F2));
+      F3 = fma(4.0, FL3, fma(2.0, dd[6 * ND + pc], F3));
+    }
+    double *out = DIR ? &fo[(fr * TX + fc) * 4] : &fo[(fr * (TX + 1) + fc) * 4];
+    out[0] = F0;
+    out[1 + DIR] = F1;
+    out[2 - DIR] = F2;
+    out[3] = F3;
   }
-  if (want_alpha) {
-    const int slot[6] = {0, 1, 3, 4, 5, 7};
-    const int dup[6] = {-1, 2, -1, -1, 6, -1};
-    block_max_atomic<6>(mx6, a.alpha_out + b * 8, slot, dup);
+  __syncthreads();
+}
+
+// One tile of a sixth-order 2D stage (see above).  sm: smem_euler2d<TX, TY>()
+// bytes; tm: tensor map of the stage input or NULL, as for euler2d_tile_gen.
+template <int TX, int TY, bool AI, bool P1, int PREC>
+__device__ __forceinline__ void euler2d_tile6(const StageArgs &a, long long b, long long tile,
+                                              bool zeroing_block, double *sm_in,
+                                              const CUtensorMap *tm) {
+  using L = Tile6<TX, TY>;
+  constexpr int R = 3, W = L::W, BW = L::BW, XO = L::XO, PB = L::PB, REG = L::REG;
+  double *const sm =
+      reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(sm_in) + 127) & ~uintptr_t(127));
+  double *const box = sm + L::kBox;
+  double *const pl = sm + L::kPl;
+
+  const long long tiles_x = (a.nx + TX - 1) / TX;
+  const long long tj = tile / tiles_x, ti = tile - tj * tiles_x;
+  const long long i0 = ti * TX, j0 = tj * TY;
+  double dt;
+  if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
+
+  const double *Ub = a.Uin + b * 4 * (a.nx * a.ny);
+  const double gm1 = a.gamma - 1.0;
+  const int tid = threadIdx.x;
+
+  // per-block constants (published by the barrier after phase 1): the
+  // reconstruction parameters of the field scales 2 and 4, 0.25 / dx, dy
+  __shared__ ReconParams s_rp[2];
+  __shared__ double s_id[2];
+  if (tid == 0) {
+    s_rp[0] = make_rp(a, 2.0);
+    s_rp[1] = make_rp(a, 4.0);
+    s_id[0] = 0.25 / a.dx;
+    s_id[1] = 0.25 / a.dy;
   }
+
+  const bool use_tma = tm != nullptr && i0 - XO >= 0 && i0 - XO + BW <= a.nx && j0 - R >= 0 &&
+                       j0 + TY + R <= a.ny;
+  if (use_tma && !tma_stage_box<TX, TY, R>(a, tm, box, b, i0, j0)) return;
+
+  // Phase 1: the cross-shaped region (tile rows with x halo, tile columns
+  // with y halo): the conserved variables into the box where TMA did not
+  // bring them, and per cell sqrt(rho), u, v, H.
+  for (int k = tid; k < REG; k += blockDim.x) {
+    const int r = k / W, c = k - r * W;
+    const bool xb = (r >= R) && (r < R + TY), yb = (c >= R) && (c < R + TX);
+    if (!(xb || yb)) continue;
+    const int ob = r * BW + c + XO - R;
+    double rho, mx, my, E;
+    long long gj, gi;
+    if (use_tma) {
+      rho = box[ob];
+      mx = box[PB + ob];
+      my = box[2 * PB + ob];
+      E = box[3 * PB + ob];
+      gi = i0 - R + c;
+      gj = j0 - R + r;
+    } else {
+      const double *src;
+      long long o, pst;
+      cell_source(a, Ub, b, i0, j0, R, r, c, src, o, pst, gj, gi);
+      rho = src[o];
+      mx = src[pst + o];
+      my = src[2 * pst + o];
+      E = src[3 * pst + o];
+      box[ob] = rho;
+      box[PB + ob] = mx;
+      box[2 * PB + ob] = my;
+      box[3 * PB + ob] = E;
+    }
+    const double rs = rsqrt_pos(rho);  // 1/sqrt(rho): gives 1/rho and sqrt(rho)
+    const double ir = rs * rs;
+    const double u = mx * ir, v = my * ir;
+    const double p = gm1 * (E - 0.5 * fma(mx, u, my * v));
+    if (!(pos_finite(rho) && pos_finite(p))) record_status(a.status, 3, a.stage, b, gj, gi);
+    pl[k] = rho * rs;
+    pl[REG + k] = u;
+    pl[2 * REG + k] = v;
+    pl[3 * REG + k] = (E + p) * ir;
+  }
+  __syncthreads();
+
+  tile6_sweep<TX, TY, AI, P1, PREC, 0>(a, b, i0, j0, gm1, sm, s_rp[0], s_rp[1]);
+  tile6_sweep<TX, TY, AI, P1, PREC, 1>(a, b, i0, j0, gm1, sm, s_rp[0], s_rp[1]);
+
+  tile2d_update<TX, TY, R>(a, b, i0, j0, dt, sm + L::kFx, sm + L::kFy, s_id[0], s_id[1],
+                           [&](int r, int c, int q) { return box[q * PB + (R + r) * BW + XO + c]; });
+}
+
+// One tile of a 2D stage of order 2R (sixth order: euler2d_tile6; 4, 8, 10:
+// euler2d_tile_gen).
+template <int TX, int TY, bool AI, bool P1, int PREC, int R = 3>
+__device__ __forceinline__ void euler2d_tile(const StageArgs &a, long long b, long long tile,
+                                             bool zeroing_block, double *sm,
+                                             const CUtensorMap *tm = nullptr) {
+  if constexpr (R == 3)
+    euler2d_tile6<TX, TY, AI, P1, PREC>(a, b, tile, zeroing_block, sm, tm);
+  else
+    euler2d_tile_gen<TX, TY, AI, P1, PREC, R>(a, b, tile, zeroing_block, sm, tm);
 }
 
 // MINB: resident blocks per SM the register allocation must allow.
@@ -584,6 +871,19 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
   const double *Ub = a.Uin + b * NC * nx;
   const double gm1 = a.gamma - 1.0;
   const int tid = threadIdx.x;
+  // per-block constants, published by the barrier after the staging: the
+  // reconstruction parameters of the field scales 2 and 4, FP32 ones, and
+  // the flux difference's factor (the faces hold 4 F for Euler, 2 F for a
+  // scalar: the split without 1/2)
+  __shared__ ReconParams s_rp[2];
+  __shared__ Recon32 s_r32;
+  __shared__ double s_idx;
+  if (tid == 0) {
+    s_rp[0] = make_rp(a, 2.0);
+    s_rp[1] = make_rp(a, 4.0);
+    s_r32 = make_r32(a);
+    s_idx = (NC == 3 ? 0.25 : 0.5) / a.dx;
+  }
 
   for (int k = tid; k < REG; k += blockDim.x) {
     const long long gi = ghost(i0 - R + k, nx, a.bc_x);
@@ -635,9 +935,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
           W[j] = project3_field(fs, q, pl[0][k], pl[1][k], pl[2][k]);
           G[j] = project3_field(fs, q, pl[6][k], pl[7][k], pl[8][k]);
         }
-        h = field_flux_f32<P1>(W, G, A, make_r32(a));
+        h = field_flux_f32<P1>(W, G, A, s_r32);
       } else {
-        const ReconParams rp = make_rp(a, q == 1 ? 2.0 : 4.0);
+        const ReconParams rp = s_rp[q == 1 ? 0 : 1];
         double W[6], G[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
@@ -667,7 +967,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
     double base = 0.0;
     if (act) {
       const double A = scalar_alpha_of(a.system, a.adv_speed, a.ustar, a.alpha_in + b * 8);
-      const ReconParams rp = make_rp(a, 2.0);
+      const ReconParams rp = s_rp[0];
       double dd[5], dw2 = 0.0;
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
@@ -697,7 +997,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             w[j] = pl[0][f + j];
             g[j] = pl[1][f + j];
           }
-          h = field_flux_f32<P1>(w, g, A, make_r32(a));
+          h = field_flux_f32<P1>(w, g, A, s_r32);
         } else if constexpr (R == 3) {
           double w[6], g[6];
 #pragma unroll
@@ -705,9 +1005,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             w[j] = pl[0][f + j];
             g[j] = pl[1][f + j];
           }
-          h = field_flux<AI, P1>(w, g, A, make_rp(a, 2.0));
+          h = field_flux<AI, P1>(w, g, A, s_rp[0]);
         } else {
-          const ReconParams rp = make_rp(a, 2.0);
+          const ReconParams rp = s_rp[0];
           double pp[N], mm[N];  // f^+ in stencil order, f^- mirrored
 #pragma unroll
           for (int j = 0; j < N; ++j) {
@@ -736,12 +1036,12 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
             project3(fs, pl[0][k], pl[1][k], pl[2][k], W[0][j], W[1][j], W[2][j]);
             project3(fs, pl[6][k], pl[7][k], pl[8][k], G[0][j], G[1][j], G[2][j]);
           }
-          const Recon32 r32 = make_r32(a);
+          const Recon32 r32 = s_r32;
           h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
           h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
           h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
         } else if constexpr (R == 3) {
-          const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
+          const ReconParams rp4 = s_rp[1], rp2 = s_rp[0];
           double W[3][6], G[3][6];
 #pragma unroll
           for (int j = 0; j < 6; ++j) {
@@ -753,7 +1053,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
           h2 = field_flux<AI, P1>(W[1], G[1], A2, rp2);
           h3 = field_flux<AI, P1>(W[2], G[2], A3, rp4);
         } else {
-          const ReconParams rp4 = make_rp(a, 4.0), rp2 = make_rp(a, 2.0);
+          const ReconParams rp4 = s_rp[1], rp2 = s_rp[0];
           double p1[N], p2[N], p3[N], m1[N], m2[N], m3[N];  // f^- mirrored
 #pragma unroll
           for (int j = 0; j < N; ++j) {
@@ -784,7 +1084,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
 
   // The faces hold 4 F (Euler, backproject3) or 2 F (a scalar: the split
   // without 1/2), so that factor goes with 1/dx.
-  const double idx = (NC == 3 ? 0.25 : 0.5) / a.dx;
+  const double idx = s_idx;
   unsigned long long m3v[3] = {0ull, 0ull, 0ull};
   const bool want_alpha = (NC == 3 || a.system >= 2) && (a.mode == 0) && (a.alpha_out != nullptr);
   if (tid < T && i0 + tid < nx) {
@@ -893,7 +1193,12 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
     // 5 = 20x12 / 128 / 3 (512 faces), 6 = 26x14 / 128 / 3 (768 faces).
     // For grids too small to fill the GPU, where a stage lasts as long as one
     // thread's chain of faces, about one face per thread: 7 = 16x8 / 256 / 1
-    // (280 faces), 8 = 8x8 / 128 / 2 (144 faces).
+    // (280 faces), 8 = 8x8 / 128 / 2 (144 faces).  The sixth-order tile
+    // sweeps the x- and then the y-faces; two shapes give every thread
+    // exactly two faces of each sweep (warp i of every block runs on the
+    // same SM sub-partition, so an uneven count leaves three of the four
+    // FP64 pipes idle at the end of a sweep): 9 = 16x15 / 128 / 3 (255 and
+    // 256 faces), 10 = 14x17 / 128 / 3 (255 and 252).
     // The other orders use 16x16 / 128 only, 3 blocks per SM at r = 2 and 2
     // at r = 4, 5 (their wider stencils need more registers).
     if constexpr (R != 3) {  // r = 2 fits the 168-register cap of 3 blocks per SM
@@ -908,6 +1213,8 @@ cudaError_t launch_stage_t(const StageArgs &a, cudaStream_t s) {
         case 6: return launch_2d<26, 14, 128, 3, AI, P1, PREC>(a, s);
         case 7: return launch_2d<16, 8, 256, 1, AI, P1, PREC>(a, s);
         case 8: return launch_2d<8, 8, 128, 2, AI, P1, PREC>(a, s);
+        case 9: return launch_2d<16, 15, 128, 3, AI, P1, PREC>(a, s);
+        case 10: return launch_2d<14, 17, 128, 3, AI, P1, PREC>(a, s);
         default: return launch_2d<kTX, kTY, kThreads2D, 1, AI, P1, PREC>(a, s);
       }
     }

@@ -341,7 +341,7 @@ def test_tile_variants_are_bitwise_identical(prec, nx, ny, monkeypatch):
     w["U"] = np.ascontiguousarray(w["U"][:, :, :ny, :nx])
     d = _fix_2d_domain(w, weno.desc_for(w, precision=prec))
     outs = []
-    for v in ("0", "1", "2", "3", "4", "5", "6", "7", "8"):
+    for v in ("0", "1", "2", "3", "4", "5", "6", "7", "8", "9", "10"):
         monkeypatch.setenv("WENO_TILE2D", v)
         U = to_gpu(w["U"])
         for _ in range(3):
