@@ -105,7 +105,7 @@ struct EngineArgs {
 constexpr int kEngineThreads = 128;
 constexpr int kEngineBlocksPerSM = 3;
 constexpr int kEngine1DCells = kEngineThreads - 1;
-constexpr int kEngineTX = 16, kEngineTY = 16;
+constexpr int kEngineTX = 16, kEngineTY = 15;  // two x- and two y-faces per thread
 size_t engine_smem_bytes();
 long long engine_tiles_of(int ndim, long long nx, long long ny);
 cudaError_t engine_prepare();  // kernel attributes; call before capturing

@@ -611,7 +611,11 @@ __device__ __forceinline__ void tile6_sweep(const StageArgs &a, long long b, lon
   //   x: pair (rr, pc), rr in [0, TY), pc in [0, W - 1): cells (R + rr, pc), (R + rr, pc + 1)
   //   y: pair (pr, cc), pr in [0, HH - 1), cc in [0, TX): cells (pr, R + cc), (pr + 1, R + cc)
   constexpr int NP = DIR ? L::NPY : L::NPX;
-  for (int k = tid; k < NP; k += blockDim.x) {
+  // the x pairs run from the block's last warp down: with phase 1 and the y
+  // pairs starting from warp 0, the partial rounds of the three loops fall
+  // on different warps (each warp's FP64 work goes to its own sub-partition)
+  const int t0 = DIR ? tid : (int)blockDim.x - 1 - tid;
+  for (int k = t0; k < NP; k += blockDim.x) {
     int rA, cA, rB, cB;
     if (DIR == 0) {
       rA = R + k / (W - 1);

@@ -307,16 +307,16 @@ def serve_continuous(engine, requests, steps_per_poll=2, keep_states=False, work
 
 
 def engine_tiles(r):
-    """Work-list tiles of a request in the engine (16 x 16 cells in 2D, 127
+    """Work-list tiles of a request in the engine (16 x 15 cells in 2D, 127
     cells in 1D)."""
     d = r.desc
     if d.ndim == 2:
-        return ((d.nx + 15) // 16) * ((d.ny + 15) // 16)
+        return ((d.nx + 15) // 16) * ((d.ny + 14) // 15)
     return (d.nx + 126) // 127
 
 
 def full_wave_tiles(device=None):
-    """Tiles the GPU runs at once: 3 blocks of 16 x 16 cells per SM."""
+    """Tiles the GPU runs at once: 3 blocks of 16 x 15 cells per SM."""
     return 3 * torch.cuda.get_device_properties(device or torch.cuda.current_device()).multi_processor_count
 
 
@@ -385,8 +385,8 @@ def serve_two_lane(engine, requests, large_tiles=None, large_workers=2, steps_pe
     at a time, first come first served, through weno_solve on a stream of
     low priority, in worker threads: `large_workers` of them, so that a
     second large solve fills the SMs the first one's last wave of tiles and
-    its host round trips leave idle (a 384^2 stage is 1.26 waves of the GPU,
-    512^2 2.25).  The oldest large solve runs on a stream of higher priority
+    its host round trips leave idle (a 384^2 stage is 1.37 waves of the GPU
+    in 16 x 15 tiles, 512^2 2.46).  The oldest large solve runs on a stream of higher priority
     than the younger ones (each solve goes in chunks of `chunk_steps` steps,
     weno_solve from the reached time, bitwise one call, and picks its stream
     per chunk), so it keeps the pace it has alone and first come first served

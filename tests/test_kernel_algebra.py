@@ -233,3 +233,84 @@ def test_cubic_newton_reciprocal_step():
     e = 1 - x * r0
     r1 = r0 + r0 * (e + e ** 2)
     assert sp.expand((1 - x * r1) - e ** 3) == 0
+
+
+def test_pairwise_weight_products():
+    # za6d forms a_k = (b_k + T) prod_{j != k} b_j pairwise: with p01 = b0 b1,
+    # p23 = b2 b3, x0 = p01 + T b1, y1 = 9 (p01 + T b0), y2 = 9 (p23 + T b3),
+    # x3 = p23 + T b2, num = p23 (y1 r1 + x0 r0) + p01 (y2 r2 + x3 r3) and
+    # den = p23 (x0 + y1) + p01 (y2 + x3) are sum d_k a_k r_k and sum d_k a_k
+    # with the linear weights d = (1, 9, 9, 1) (times 20).
+    b = sp.symbols("b0:4", positive=True)
+    r = sp.symbols("r0:4")
+    T = sp.symbols("T", positive=True)
+    dk = [1, 9, 9, 1]
+    a = [(b[k] + T) * sp.prod([b[j] for j in range(4) if j != k]) for k in range(4)]
+    p01, p23 = b[0] * b[1], b[2] * b[3]
+    x0, y1 = p01 + T * b[1], 9 * (p01 + T * b[0])
+    y2, x3 = 9 * (p23 + T * b[3]), p23 + T * b[2]
+    num = p23 * (y1 * r[1] + x0 * r[0]) + p01 * (y2 * r[2] + x3 * r[3])
+    den = p23 * (x0 + y1) + p01 * (y2 + x3)
+    assert sp.expand(num - sum(dk[k] * a[k] * r[k] for k in range(4))) == 0
+    assert sp.expand(den - sum(dk[k] * a[k] for k in range(4))) == 0
+
+
+def test_centre_values_back_project_to_the_physical_flux():
+    # The 2D sixth-order kernel reconstructs from differences only and leaves
+    # out the centre values g_i + g_{i+1} = P(F_i + F_{i+1}) of every field
+    # (P: project4, the scaled left eigenvectors 2 l1, l2, l3, 2 l4).  Their
+    # back-projection R (c1, 2 c2, 2 c3, c4) is 2 (F_i + F_{i+1}) for any
+    # F_i + F_{i+1} (R L = I), which the kernel adds as 4 F_i + 2 (F_{i+1} - F_i).
+    un, ut, c, g = sp.symbols("u_n u_t c gamma", positive=True)
+    q2 = un ** 2 + ut ** 2
+    H = c ** 2 / (g - 1) + q2 / 2
+    b1 = (g - 1) / c ** 2
+    b2 = b1 * q2 / 2
+
+    def project4(rho, mn, mt, E):
+        sx = un * mn + ut * mt - E
+        z = b2 * rho - b1 * sx
+        tc = (un * rho - mn) / c
+        return [z + tc, rho - z, mt - ut * rho, z - tc]
+
+    def backproject4(h1, h2, h3, h4):
+        h14 = h1 + h4
+        S = 2 * h2 + h14
+        D = h4 - h1
+        return sp.Matrix([S, un * S + c * D, ut * S + 2 * h3,
+                          H * h14 + un * c * D + q2 * h2 + ut * 2 * h3])
+
+    FL = sp.symbols("FL0:4")
+    dF = sp.symbols("dF0:4")
+    FR = [FL[q] + dF[q] for q in range(4)]
+    cvals = [x + y for x, y in zip(project4(*FL), project4(*FR))]
+    kern = sp.Matrix([4 * FL[q] + 2 * dF[q] for q in range(4)])
+    assert sp.simplify(backproject4(*cvals) - kern) == sp.zeros(4, 1)
+    # the projection is linear: the differences of projected states are the
+    # projected differences (what the kernel projects)
+    U0, U1 = sp.symbols("a0:4"), sp.symbols("c0:4")
+    lhs = [y - x for x, y in zip(project4(*U0), project4(*U1))]
+    rhs = project4(*[U1[q] - U0[q] for q in range(4)])
+    assert all(sp.expand(x - y) == 0 for x, y in zip(lhs, rhs))
+
+
+def test_normal_flux_from_staged_values():
+    # the kernel stages u_n and H = (E + p) / rho and forms p = rho H - E,
+    # F1 = m_n u_n + p, F2 = m_t u_n, F3 = H m_n (eq. (25) in the normal frame)
+    rho, un, ut, p, g = sp.symbols("rho u_n u_t p gamma", positive=True)
+    mn, mt = rho * un, rho * ut
+    E = p / (g - 1) + rho * (un ** 2 + ut ** 2) / 2
+    H = (E + p) / rho
+    assert sp.simplify(rho * H - E - p) == 0
+    assert sp.simplify(H * mn - (E + p) * un) == 0
+
+
+def test_third_order_reciprocal_square_root_step():
+    # r1 = r (1 + e/2 + 3 e^2 / 8), e = 1 - x r^2: the series of (1 - e)^(-1/2)
+    # to second order, so r1 sqrt(x) = 1 - (5/16) e^3 + O(e^4): a seed within
+    # 2^-22 gives 1/sqrt(x) to about 2^-64 before the final roundings
+    e = sp.symbols("e")
+    # r sqrt(x) = (1 - e)^(1/2) exactly
+    r1_sqrtx = sp.sqrt(1 - e) * (1 + e / 2 + sp.Rational(3, 8) * e ** 2)
+    ser = sp.series(r1_sqrtx, e, 0, 4).removeO()
+    assert sp.expand(ser - (1 - sp.Rational(5, 16) * e ** 3)) == 0
