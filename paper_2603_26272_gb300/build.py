@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libweno.so")
 SOURCES = ["weno_kernels.cu", "weno_orders.cu", "weno_api.cu", "weno_noalloc.cu", "weno_engine.cu",
            "weno_peak.cu"]
-HEADERS = ["weno_device.cuh", "weno_tiles.cuh", "weno_internal.h"]
+HEADERS = ["weno_device.cuh", "weno_tiles.cuh", "weno_tiles1d.cuh", "weno_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
