@@ -8,11 +8,26 @@
 // 1D stage kernel: NC = 3 (Euler) or 1 (scalar advection).  Tile of
 // kT1 = 127 cells, 128 faces, one face per thread.
 // Planes: 0 rho, 1 m, 2 E, 3 u, 4 H, 5 sqrt(rho), 6-8 F  (advection: 0 u).
+// Sixth-order Euler projects differences of adjacent cells, as the 2D
+// kernel does (euler2d_tile6): dd holds per cell pair d rho, dm, dE, dF1, dF2
+// (dF0 = dm), and the centre values come back as 4 F_i + 2 (F_{i+1} - F_i)
+// after the back-projection.
 // ---------------------------------------------------------------------------
+// The centre values of a sixth-order 1D Euler face between cells L and L+1:
+// 4 F_hat += 2 (F_L + F_{L+1}) = 4 F_L + 2 dF of pair L (R L = I).
+__device__ __forceinline__ void add_centre3(double FL0, double FL1, double FL2, const double *dd,
+                                            int nd, int pair, double &F0, double &F1,
+                                            double &F2) {
+  F0 = fma(4.0, FL0, fma(2.0, dd[nd + pair], F0));
+  F1 = fma(4.0, FL1, fma(2.0, dd[3 * nd + pair], F1));
+  F2 = fma(4.0, FL2, fma(2.0, dd[4 * nd + pair], F2));
+}
+
 template <int NC, int T, int R = 3, int LANES = 1>
 constexpr size_t smem_line1d() {
   return sizeof(double) * (((NC == 3) ? 9 : 2) * (T + 2 * R) + (T + 1) * NC +
-                           (LANES > 1 ? (T + 1) * NC : 0));
+                           (LANES > 1 ? (T + 1) * NC : 0) +
+                           ((NC == 3 && R == 3) ? 5 * (T + 2 * R - 1) : 0));
 }
 
 // One tile of T cells (T + 1 faces) of a 1D stage with a stencil of
@@ -34,6 +49,9 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
   double(*pl)[REG] = reinterpret_cast<double(*)[REG]>(sm);
   double(*fl)[NC] = reinterpret_cast<double(*)[NC]>(sm + NP * REG);
   double *const hb = sm + NP * REG + (T + 1) * NC;  // LANES > 1: per-field fluxes
+  constexpr bool kDiff = (NC == 3 && R == 3);
+  constexpr int ND = REG - 1;  // cell pairs of the tile
+  double *const dd = hb + (LANES > 1 ? (T + 1) * NC : 0);  // kDiff: [5][ND]
   const long long i0 = tile * T;
   double dt;
   if (!stage_control(a, b, tile == 0, zeroing_block, dt)) return;
@@ -82,6 +100,16 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
     }
   }
   __syncthreads();
+  if constexpr (kDiff) {
+    for (int k = tid; k < ND; k += blockDim.x) {
+      dd[k] = pl[0][k + 1] - pl[0][k];
+      dd[ND + k] = pl[1][k + 1] - pl[1][k];
+      dd[2 * ND + k] = pl[2][k + 1] - pl[2][k];
+      dd[3 * ND + k] = pl[7][k + 1] - pl[7][k];
+      dd[4 * ND + k] = pl[8][k + 1] - pl[8][k];
+    }
+    __syncthreads();
+  }
 
   if constexpr (LANES == 3) {
     // one characteristic field per thread; the field-0 thread back-projects
@@ -97,32 +125,24 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
       double A = bits2d(al[q]);
       if (a.alpha_single) A = fmax(fmax(bits2d(al[0]), bits2d(al[1])), bits2d(al[2]));
       double h;
-      if constexpr (PREC == 1) {
-        double W[6], G[6];
+      double dW[5], dG[5];  // the field's projected differences over pairs f .. f+4
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const int k = f + j;
-          W[j] = project3_field(fs, q, pl[0][k], pl[1][k], pl[2][k]);
-          G[j] = project3_field(fs, q, pl[6][k], pl[7][k], pl[8][k]);
-        }
-        h = field_flux_f32<P1>(W, G, A, s_r32);
-      } else {
-        const ReconParams rp = s_rp[q == 1 ? 0 : 1];
-        double W[6], G[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const int k = f + j;
-          W[j] = project3_field(fs, q, pl[0][k], pl[1][k], pl[2][k]);
-          G[j] = project3_field(fs, q, pl[6][k], pl[7][k], pl[8][k]);
-        }
-        h = field_flux<AI, P1>(W, G, A, rp);
+      for (int j = 0; j < 5; ++j) {
+        const int k = f + j;
+        dW[j] = project3_field(fs, q, dd[k], dd[ND + k], dd[2 * ND + k]);
+        dG[j] = project3_field(fs, q, dd[ND + k], dd[3 * ND + k], dd[4 * ND + k]);
       }
+      if constexpr (PREC == 1)
+        h = field_flux_f32d<P1>(dW, dG, A, s_r32);
+      else
+        h = field_flux_d<AI, P1>(dW, dG, A, s_rp[q == 1 ? 0 : 1]);
       hb[3 * f + q] = h;
     }
     __syncthreads();
     if (act && q == 0) {
       double F0, F1, F2;
       backproject3(fs, hb[3 * f], hb[3 * f + 1], hb[3 * f + 2], F0, F1, F2);
+      add_centre3(pl[6][f + 2], pl[7][f + 2], pl[8][f + 2], dd, ND, f + 2, F0, F1, F2);
       fl[f][0] = F0;
       fl[f][1] = F1;
       fl[f][2] = F2;
@@ -198,30 +218,24 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
         double A1 = bits2d(al[0]), A2 = bits2d(al[1]), A3 = bits2d(al[2]);
         if (a.alpha_single) A1 = A2 = A3 = fmax(fmax(A1, A2), A3);
         double h1, h2, h3;
-        if constexpr (PREC == 1) {
-          double W[3][6], G[3][6];
+        if constexpr (R == 3) {
+          double dW[3][5], dG[3][5];  // projected differences over pairs f .. f+4
 #pragma unroll
-          for (int j = 0; j < 6; ++j) {
+          for (int j = 0; j < 5; ++j) {
             const int k = f + j;
-            project3(fs, pl[0][k], pl[1][k], pl[2][k], W[0][j], W[1][j], W[2][j]);
-            project3(fs, pl[6][k], pl[7][k], pl[8][k], G[0][j], G[1][j], G[2][j]);
+            project3(fs, dd[k], dd[ND + k], dd[2 * ND + k], dW[0][j], dW[1][j], dW[2][j]);
+            project3(fs, dd[ND + k], dd[3 * ND + k], dd[4 * ND + k], dG[0][j], dG[1][j],
+                     dG[2][j]);
           }
-          const Recon32 r32 = s_r32;
-          h1 = field_flux_f32<P1>(W[0], G[0], A1, r32);
-          h2 = field_flux_f32<P1>(W[1], G[1], A2, r32);
-          h3 = field_flux_f32<P1>(W[2], G[2], A3, r32);
-        } else if constexpr (R == 3) {
-          const ReconParams rp4 = s_rp[1], rp2 = s_rp[0];
-          double W[3][6], G[3][6];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            const int k = f + j;
-            project3(fs, pl[0][k], pl[1][k], pl[2][k], W[0][j], W[1][j], W[2][j]);
-            project3(fs, pl[6][k], pl[7][k], pl[8][k], G[0][j], G[1][j], G[2][j]);
+          if constexpr (PREC == 1) {
+            h1 = field_flux_f32d<P1>(dW[0], dG[0], A1, s_r32);
+            h2 = field_flux_f32d<P1>(dW[1], dG[1], A2, s_r32);
+            h3 = field_flux_f32d<P1>(dW[2], dG[2], A3, s_r32);
+          } else {
+            h1 = field_flux_d<AI, P1>(dW[0], dG[0], A1, s_rp[1]);
+            h2 = field_flux_d<AI, P1>(dW[1], dG[1], A2, s_rp[0]);
+            h3 = field_flux_d<AI, P1>(dW[2], dG[2], A3, s_rp[1]);
           }
-          h1 = field_flux<AI, P1>(W[0], G[0], A1, rp4);
-          h2 = field_flux<AI, P1>(W[1], G[1], A2, rp2);
-          h3 = field_flux<AI, P1>(W[2], G[2], A3, rp4);
         } else {
           const ReconParams rp4 = s_rp[1], rp2 = s_rp[0];
           double p1[N], p2[N], p3[N], m1[N], m2[N], m3[N];  // f^- mirrored
@@ -244,6 +258,7 @@ __device__ __forceinline__ void line1d_tile(const StageArgs &a, long long b, lon
         }
         double F0, F1, F2;
         backproject3(fs, h1, h2, h3, F0, F1, F2);
+        if constexpr (R == 3) add_centre3(pl[6][kL], pl[7][kL], pl[8][kL], dd, ND, kL, F0, F1, F2);
         fl[f][0] = F0;
         fl[f][1] = F1;
         fl[f][2] = F2;
