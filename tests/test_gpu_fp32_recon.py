@@ -124,3 +124,23 @@ def test_fp32_recon_power_parameter_next_to_flat_substencils(p):
     L_g = weno.rhs(d, torch.from_numpy(np.ascontiguousarray(w["U"])).cuda()).cpu().numpy()
     assert np.isfinite(L_g).all()
     assert rel_linf(L_g, L_o) <= STAGE_TOL_F32
+
+
+@pytest.mark.parametrize("scale_exp", [-200, 200, 400])
+@pytest.mark.parametrize("name", ["quadrant", "shock_density"])
+def test_fp32_recon_data_beyond_fp32_range(scale_exp, name):
+    """The FP32 part takes a stencil's differences scaled by a common power
+    of two, so data whose magnitude lies far outside FP32's range (2^-200,
+    2^200, 2^400) reconstruct as well as O(1) data.  The Euler right-hand
+    side is homogeneous of degree 1 in U and every scaling in the path is by
+    a power of two, so L(2^k U) = 2^k L(U) to rounding; and against the FP64
+    oracle at the scaled data within the mode's per-stage bound."""
+    w = dict(CASES)[name]
+    d = weno.desc_for(w, precision="fp32_recon")
+    c = 2.0 ** scale_exp
+    U = np.ascontiguousarray(w["U"])
+    L1 = weno.rhs(d, torch.from_numpy(U).cuda()).cpu().numpy()
+    Lc = weno.rhs(d, torch.from_numpy(U * c).cuda()).cpu().numpy()
+    assert np.isfinite(Lc).all()
+    assert rel_linf(Lc / c, L1) <= 1e-14
+    assert rel_linf(Lc, oracle.rhs(grid_of(d), U * c)) <= STAGE_TOL_F32
