@@ -133,8 +133,13 @@ def test_fp32_recon_data_beyond_fp32_range(scale_exp, name):
     of two, so data whose magnitude lies far outside FP32's range (2^-200,
     2^200, 2^400) reconstruct as well as O(1) data.  The Euler right-hand
     side is homogeneous of degree 1 in U and every scaling in the path is by
-    a power of two, so L(2^k U) = 2^k L(U) to rounding; and against the FP64
-    oracle at the scaled data within the mode's per-stage bound."""
+    a power of two, so L(2^k U) = 2^k L(U) to rounding.  Against the FP64
+    oracle at the scaled data within the mode's per-stage bound where the
+    data's variation is far above mu_0 (2^200, 2^400): at 2^-200 it is
+    ~1e-61, below mu_0 = 1e-40, where the mu_0 term of eq. (22) dominates
+    the descaler and the FP64 weights are no longer those of the scaled-up
+    data, while this mode normalises by the stencil's variation alone
+    (reading A-2)."""
     w = dict(CASES)[name]
     d = weno.desc_for(w, precision="fp32_recon")
     c = 2.0 ** scale_exp
@@ -143,4 +148,5 @@ def test_fp32_recon_data_beyond_fp32_range(scale_exp, name):
     Lc = weno.rhs(d, torch.from_numpy(U * c).cuda()).cpu().numpy()
     assert np.isfinite(Lc).all()
     assert rel_linf(Lc / c, L1) <= 1e-14
-    assert rel_linf(Lc, oracle.rhs(grid_of(d), U * c)) <= STAGE_TOL_F32
+    if scale_exp > 0:
+        assert rel_linf(Lc, oracle.rhs(grid_of(d), U * c)) <= STAGE_TOL_F32
