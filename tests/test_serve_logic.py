@@ -119,3 +119,33 @@ def test_fast_light_marks_cheap_requests_only():
     eng = FakeEngine(capacity=100)
     serve.serve_continuous(eng, rs, steps_per_poll=1, fast="light", fast_units=50.0)
     assert sorted(s for s, f in eng.fast_log if f) == [1, 2]
+
+
+def test_engine_tile_count_matches_the_library_constants():
+    """serve.engine_tiles decides which solves fill the GPU alone from the
+    engine's tile shape; the shape is a constant of the CUDA library
+    (kEngineTX, kEngineTY, kEngine1DCells in csrc/weno_internal.h), so the
+    two must agree."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(serve.__file__), "csrc", "weno_internal.h")).read()
+    tx = int(re.search(r"kEngineTX\s*=\s*(\d+)", src).group(1))
+    ty = int(re.search(r"kEngineTY\s*=\s*(\d+)", src).group(1))
+    threads = int(re.search(r"kEngineThreads\s*=\s*(\d+)", src).group(1))
+    cells1d = threads - 1 if re.search(r"kEngine1DCells\s*=\s*kEngineThreads\s*-\s*1", src) \
+        else int(re.search(r"kEngine1DCells\s*=\s*(\d+)", src).group(1))
+
+    @dataclass
+    class D:
+        ndim: int
+        nx: int
+        ny: int
+
+    @dataclass
+    class R:
+        desc: object
+
+    for nx, ny in [(128, 128), (384, 384), (1024, 1024), (100, 37)]:
+        assert serve.engine_tiles(R(D(2, nx, ny))) == -(-nx // tx) * -(-ny // ty)
+    for n in (256, 1600, 16384):
+        assert serve.engine_tiles(R(D(1, n, 1))) == -(-n // cells1d)
